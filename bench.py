@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched inference-machine simulation on B300.
+
+Workload (default): the batched 2D toric sweep -- L in {16, 32, 64, 128}, 11
+error rates p in 0.02..0.12, FP32 min-sum, check-centric feedback, one BP
+sweep per tick (dt = tau = 0.1), tick budget 40L, all points mixed in one
+persistent launch.  One step = one lim_run_batch over ``--shots`` fresh shots
+of every point (shot ids advance every step), run to completion.
+
+Prints one JSON line.  ``value`` is shot-ticks per second (ticks executed,
+summed over shots, divided by device time of the steps); msg-updates/s, the
+roofline of the batch kernel, the oracle's CPU rate, the end-to-end rate
+through the public API (records and tallies read back to the host every
+step), the SM clocks seen during the timed region and the number of our
+kernel launches are reported alongside.
+
+``--impl reference`` times the CPU oracle (the plain reference implementation)
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2609_38139_b300 import inputs as I  # noqa: E402
+
+METRIC = "shot-ticks/s & msg-updates/s vs HBM/SMEM roofline; batched+lowprec vs plain at equal P_L"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6400.0
+
+
+def workload(name: str, shots: int):
+    w = I.WORKLOADS[name]
+    pts = []
+    for fam, size, p, pid in I.workload_points(name):
+        pts.append(dict(family=fam, size=size, p=p, point_id=pid, shots=shots,
+                        T=I.tick_budget(w["budget"], size)))
+    # most expensive points first: the queue hands out work in this order
+    pts.sort(key=lambda d: (-I.make_code(d["family"], d["size"]).E * d["T"], -d["p"]))
+    return w, pts
+
+
+def lib_params(L, w, name, prec, variant="auto"):
+    if name == "rep2000_p045":
+        return L.params(feedback="bit_discrete", precision=prec, q=w["q"], clamp=w["clamp"],
+                        tick_budget=8001, variant=variant)
+    qs = 0.25 if prec == "i8" else 2 ** -6
+    return L.params(precision=prec, quant_scale=qs, q=w["q"], clamp=w["clamp"], tau=w["tau"],
+                    dt_tick=w["dt_tick"], sweeps_per_tick=w["K"], tick_budget=w.get("T", 0) or 1,
+                    variant=variant)
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip() == "Active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peak_hbm():
+    try:
+        d = json.load(open(PEAKS_FILE))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def cpu_baseline(name: str, prec: str, seconds: float = 15.0, threads: int = 0):
+    """The oracle timed on this host's cores on a bounded sample of the workload:
+    shots of every point in turn (same keyed shot ids as the GPU's step 0) until
+    about ``seconds`` of wall time have passed."""
+    import oracle as O
+    from concurrent.futures import ThreadPoolExecutor
+    w, pts = workload(name, 1)
+    threads = threads or (os.cpu_count() or 1)
+    codes = {}
+    t0 = time.perf_counter()
+    ticks = 0
+    shots = 0
+    upd = 0
+    jobs = []
+    for d in sorted(pts, key=lambda d: d["point_id"]):
+        key = (d["family"], d["size"])
+        if key not in codes:
+            c = I.make_code(*key)
+            codes[key] = (c, O.OracleCode.from_code(c))
+        jobs.append(d)
+    # one shot per point per round, all points, over `threads` threads
+    rnd = 0
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        while time.perf_counter() - t0 < seconds:
+            futs = []
+            for d in jobs:
+                c, oc = codes[(d["family"], d["size"])]
+                op = O.params(precision=prec if prec in ("f32", "f16", "bf16", "i16", "i8") else "f64",
+                              quant_scale=2 ** -6, q=w["q"], clamp=w["clamp"], tau=w["tau"],
+                              dt_tick=w["dt_tick"], sweeps_per_tick=w["K"], tick_budget=d["T"])
+                futs.append((c, ex.submit(O.run_shots, oc, op, d["p"], 0, d["point_id"], rnd, 1)))
+            for c, f in futs:
+                r = f.result()
+                ticks += int(r["ticks"].sum())
+                upd += int(r["sweeps"].sum()) * 2 * c.E
+                shots += len(r)
+            rnd += 1
+    dt = time.perf_counter() - t0
+    return {"value": ticks / dt, "unit": "shot-ticks/s", "cores": threads, "kind": "oracle",
+            "msg_updates_per_s": upd / dt,
+            "sample": f"{shots} shots ({rnd} per point, every point of the workload, same shot ids "
+                      f"as the GPU's first step), {prec} oracle, {dt:.1f} s wall"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    steps = []
+    for _ in range(args.warmup):
+        cpu_baseline(args.workload, args.precision, seconds=max(1.0, args.ref_seconds / 4))
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(args.workload, args.precision, seconds=args.ref_seconds)
+        steps.append(last)
+    wall = time.perf_counter() - t0
+    val = statistics.mean(s["value"] for s in steps)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "shot-ticks/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * wall / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": args.workload, "parallelism": "host threads"},
+            "cpu_baseline": {"value": val, "unit": "shot-ticks/s", "cores": last["cores"],
+                             "kind": "oracle", "sample": last["sample"]},
+            "e2e": {"value": val, "unit": "shot-ticks/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="toric2d_sweep")
+    ap.add_argument("--precision", default="f32")
+    ap.add_argument("--variant", default="auto")
+    ap.add_argument("--shots", type=int, default=16, help="shots per point per step")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--block-threads", type=int, default=0)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2609_38139_b300 import lim as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    ctx = L.Context(local)
+    w, pts = workload(args.workload, args.shots)
+    codes = {}
+    for d in pts:
+        key = (d["family"], d["size"])
+        if key not in codes:
+            codes[key] = ctx.from_inputs(I.make_code(*key))
+    prm = lib_params(L, w, args.workload, args.precision, args.variant)
+    prm.block_threads = args.block_threads
+    prm.blocks_per_sm = args.blocks_per_sm
+    # weak scaling: every rank runs its own disjoint shot ids of every point
+    def step_points(step):
+        base = (step * world + rank) * args.shots
+        return [(codes[(d["family"], d["size"])], d["p"], d["shots"], base, d["point_id"], d["T"])
+                for d in pts]
+
+    batch = L.Batch(ctx, step_points(0), prm, records=True)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 126 MB L2
+    step_id = [0]
+
+    def run_step(timed_events=None):
+        batch.points = step_points(step_id[0])
+        batch.pts = L._points(batch.points)
+        step_id[0] += 1
+        flush.fill_(step_id[0] & 0xFF)  # evict L2 between steps (outside the timed window)
+        if timed_events:
+            timed_events[0].record(stream)
+        batch.run(0, stream)
+        if timed_events:
+            timed_events[1].record(stream)
+
+    for _ in range(args.warmup):
+        run_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    tallies = []
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        run_step(evs[i])
+        tallies.append(batch.tally.clone())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = sum(ms)
+    ticks = upd = shots = fails = 0
+    for t in tallies:
+        arr = np.frombuffer(t.cpu().numpy().tobytes(), dtype=L.TALLY_DTYPE)
+        ticks += int(arr["ticks"].sum())
+        upd += int(arr["msg_updates"].sum())
+        shots += int(arr["shots"].sum())
+        fails += int(arr["failures"].sum())
+        assert int(arr["errors"].sum()) == 0, "device-side error counter set"
+    if dist:
+        t = torch.tensor([tot_ms, ticks, upd, shots], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        tot_ms = float(mx[0])
+        ticks, upd, shots = int(t[1]), int(t[2]), int(t[3])
+    value = ticks / (tot_ms / 1000.0)
+    upd_rate = upd / (tot_ms / 1000.0)
+    bpm = L.MSG_BYTES[args.precision]
+    hbm, hbm_src = peak_hbm()
+    achieved = upd * 2 * bpm / (tot_ms / 1000.0) / 1e9 / world
+    line = {"metric": METRIC, "value": value, "unit": "shot-ticks/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": args.workload, "codes": "toric2d L=16,32,64,128",
+                       "points": len(pts), "shots_per_point_per_step": args.shots,
+                       "shots_per_step": shots // max(1, args.steps) // world,
+                       "rule": "minsum", "feedback": "check_move", "sweeps_per_tick": w["K"],
+                       "tick_budget": "40L", "variant": args.variant,
+                       "l2": "flushed between steps (256 MiB write, outside the timed window)",
+                       "parallelism": f"replicas x{world}, disjoint shot ids"},
+            "msg_updates_per_s": upd_rate,
+            "ler_sample": fails / max(1, shots),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)",
+                         "kernel": "batch_kernel (persistent)",
+                         "algorithmic_bytes": "2 x msg bytes per message update (read old, write new)"},
+            "clocks": clk, "gpu_launches": args.steps}
+    # end to end through the public API: run + read records and tallies back
+    if not args.no_e2e:
+        rec_host = torch.empty(batch.rec.numel(), dtype=torch.uint8, pin_memory=True)
+        tal_host = torch.empty(batch.tally.numel(), dtype=torch.uint8, pin_memory=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e_ticks = 0
+        for i in range(args.steps):
+            batch.points = step_points(step_id[0])
+            batch.pts = L._points(batch.points)
+            step_id[0] += 1
+            batch.run(0, stream)
+            rec_host.copy_(batch.rec, non_blocking=True)
+            tal_host.copy_(batch.tally, non_blocking=True)
+            torch.cuda.synchronize()
+            arr = np.frombuffer(tal_host.numpy().tobytes(), dtype=L.TALLY_DTYPE)
+            e_ticks += int(arr["ticks"].sum())
+        e_dt = time.perf_counter() - t0
+        line["e2e"] = {"value": e_ticks / e_dt * world, "unit": "shot-ticks/s",
+                       "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": int(batch.rec.numel() + batch.tally.numel()),
+                       "note": "noise is sampled on the device (part of the method); the point "
+                               "list travels as launch parameters; records and tallies are read back"}
+        line["gpu_launches"] = args.steps
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.precision, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

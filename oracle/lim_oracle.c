@@ -191,8 +191,12 @@ static double w_store(const wk *w, double x) {
 static double w_relax(const wk *w, double m_old, double m_new) {
   if (w->alpha == 1.0) return m_new;
   if (w->is_int) {
+    /* m + alpha (m' - m) with alpha = A / 2^15, rounded half away from zero: an
+     * odd function of (m, m'), so the update keeps the gauge covariance of BP
+     * (Proposition of Sec. S2) exactly. */
     double d = m_new - m_old;
-    return m_old + floor((w->A * d + 16384.0) / 32768.0);
+    double q = floor((w->A * fabs(d) + 16384.0) / 32768.0);
+    return m_old + (d < 0 ? -q : q);
   }
   return w_add(w, m_old, w_mul(w, w->alpha_w, w_sub(w, m_new, m_old)));
 }

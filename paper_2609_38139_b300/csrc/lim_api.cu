@@ -1,0 +1,571 @@
+// lim_api.cu -- the extern "C" entry points of include/lim.h: context, codes,
+// the derivation of the method's scalars in the working arithmetic, launch
+// planning and the launches themselves.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lim_internal.h"
+
+struct lim_ctx {
+  int device;
+  int num_sms;
+  int smem_optin;      // max dynamic shared memory per block
+  int smem_per_sm;
+};
+
+struct lim_code {
+  lim_ctx *ctx;
+  lim::HostCode host;
+  lim::DevCode dev;
+  void *dmem;
+};
+
+namespace lim {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+
+constexpr size_t kWsHeader = 4096;  // queue counter + a tally used by lim_trace
+
+int cuda_fail(cudaError_t err, const char *what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(err));
+  return LIM_E_CUDA;
+}
+
+int bad(int st, const char *msg) {
+  set_error(msg);
+  return st;
+}
+
+double round_half_away(double x) { return x < 0 ? -std::floor(-x + 0.5) : std::floor(x + 0.5); }
+
+uint64_t prob_threshold(double p) {
+  if (p >= 1.0) return 4294967296ull;
+  if (p <= 0.0) return 0;
+  return (uint64_t)std::floor(p * 4294967296.0);
+}
+
+// The method's scalars in the working arithmetic (binary32 values or integer
+// steps).  Every definition is the paper's quantity rounded once:
+//   pi = log(q/(1-q)) (Sec. S1), theta_d = -log(d-1) (Evidence >= 1/d, Algorithm 1),
+//   alpha = dt/(K tau) (Euler step of the relaxation ODE), rho = 1 - exp(-dt)
+//   (probability that a rate-1 clock rings within a tick).
+int derive(const lim_params *p, DevParams &o) {
+  if (!p) return bad(LIM_E_INVAL, "null params");
+  std::memset(&o, 0, sizeof(o));
+  if (p->rule != LIM_RULE_MINSUM && p->rule != LIM_RULE_SUMPRODUCT) return bad(LIM_E_INVAL, "bad rule");
+  if (p->feedback != LIM_FB_CHECK_MOVE && p->feedback != LIM_FB_BIT_DISCRETE)
+    return bad(LIM_E_INVAL, "bad feedback");
+  if (p->precision < LIM_PREC_F32 || p->precision > LIM_PREC_I8) return bad(LIM_E_INVAL, "bad precision");
+  const bool is_int = p->precision == LIM_PREC_I16 || p->precision == LIM_PREC_I8;
+  if (is_int && p->rule != LIM_RULE_MINSUM)
+    return bad(LIM_E_UNSUPPORTED, "integer messages support min-sum only");
+  if (!(p->q > 0.0 && p->q < 1.0)) return bad(LIM_E_INVAL, "q must be in (0,1)");
+  if (!(p->clamp > 0.0)) return bad(LIM_E_INVAL, "clamp must be > 0");
+  if (p->sweeps_per_tick < 1) return bad(LIM_E_INVAL, "sweeps_per_tick must be >= 1");
+  if (p->tick_budget < 0) return bad(LIM_E_INVAL, "tick_budget must be >= 0");
+  double alpha = 1.0;
+  if (p->tau > 0.0 && p->dt_tick > 0.0) alpha = p->dt_tick / (p->sweeps_per_tick * p->tau);
+  if (!(alpha > 0.0 && alpha <= 1.0)) return bad(LIM_E_INVAL, "alpha = dt/(K tau) must be in (0,1]");
+  o.rule = p->rule;
+  o.feedback = p->feedback;
+  o.prec = p->precision;
+  o.K = p->sweeps_per_tick;
+  o.gauge_on_move = (p->feedback == LIM_FB_CHECK_MOVE) && p->gauge_on_move ? 1 : 0;
+  o.alpha_is_one = alpha == 1.0;
+  const double pi = std::log(p->q / (1.0 - p->q));
+  if (is_int) {
+    if (!(p->quant_scale > 0.0)) return bad(LIM_E_INVAL, "quant_scale must be > 0");
+    const double qmax = p->precision == LIM_PREC_I16 ? 32767.0 : 127.0;
+    const double d = p->quant_scale;
+    o.pi_q = (int32_t)round_half_away(pi / d);
+    o.clamp_q = (int32_t)std::min(qmax, round_half_away(p->clamp / d));
+    o.A = (int32_t)round_half_away(alpha * 32768.0);
+    for (int k = 0; k <= kMaxDeg; k++)
+      o.theta_q[k] = k <= 1 ? INT_MAX : (int32_t)std::ceil(-std::log((double)(k - 1)) / d);
+  } else {
+    o.pi_f = (float)pi;
+    o.clamp_f = (float)p->clamp;
+    o.alpha_f = (float)alpha;
+    for (int k = 0; k <= kMaxDeg; k++)
+      o.theta_f[k] = k <= 1 ? INFINITY : (float)(-std::log((double)(k - 1)));
+  }
+  const double rho = p->ring_prob >= 0.0 ? p->ring_prob : 1.0 - std::exp(-p->dt_tick);
+  o.ring_thr = rho >= 1.0 ? 4294967296ull : (rho <= 0.0 ? 0 : (uint64_t)std::floor(rho * 4294967296.0));
+  return LIM_OK;
+}
+
+struct Plan {
+  int warp = 0;
+  int block = 0;
+  int grid = 0;
+  size_t smem = 0;
+  size_t team_smem = 0;
+  size_t slot_bytes = 0;
+  size_t n_teams = 0;
+  std::vector<const lim_code *> codes;
+  std::vector<int> code_of_point;
+  std::vector<uint32_t> arena_smem;  // per code
+  size_t workspace = 0;
+};
+
+int make_plan(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+              const DevParams &dp, Plan &pl) {
+  if (!ctx) return bad(LIM_E_INVAL, "null context");
+  if (ctx->device < 0) return bad(LIM_E_INVAL, "host-only context cannot run kernels");
+  if (!pts || npts == 0) return bad(LIM_E_INVAL, "no points");
+  if (npts > LIM_MAX_POINTS) return bad(LIM_E_UNSUPPORTED, "more than LIM_MAX_POINTS points");
+  for (uint32_t i = 0; i < npts; i++) {
+    const lim_code *c = pts[i].code;
+    if (!c) return bad(LIM_E_INVAL, "point without code");
+    if (c->ctx != ctx) return bad(LIM_E_INVAL, "code belongs to another context");
+    if (pts[i].point_id >= (1u << 28)) return bad(LIM_E_INVAL, "point_id must be < 2^28");
+    if ((uint64_t)pts[i].shot0 + pts[i].shots > (1ull << 32)) return bad(LIM_E_INVAL, "shot ids exceed 2^32");
+    if (!(pts[i].p >= 0.0 && pts[i].p <= 1.0)) return bad(LIM_E_INVAL, "p must be in [0,1]");
+    auto it = std::find(pl.codes.begin(), pl.codes.end(), c);
+    if (it == pl.codes.end()) {
+      if (pl.codes.size() == LIM_MAX_CODES) return bad(LIM_E_UNSUPPORTED, "more than LIM_MAX_CODES codes");
+      pl.codes.push_back(c);
+      pl.code_of_point.push_back((int)pl.codes.size() - 1);
+    } else {
+      pl.code_of_point.push_back((int)(it - pl.codes.begin()));
+    }
+  }
+  std::vector<CodeLayout> lay;
+  size_t max_bits = 0, max_all = 0;
+  int max_E = 0;
+  for (auto *c : pl.codes) {
+    lay.push_back(code_layout(c->dev, dp.prec));
+    max_bits = std::max(max_bits, lay.back().bits_bytes);
+    max_all = std::max(max_all, lay.back().bits_bytes + lay.back().arena_bytes);
+    max_E = std::max(max_E, c->dev.E);
+  }
+  int variant = prm->variant;
+  if (variant == LIM_VARIANT_PLAIN) return bad(LIM_E_UNSUPPORTED, "plain variant not built");
+  if (variant == LIM_VARIANT_AUTO) variant = (max_all <= 24 * 1024 && max_E <= 2048) ? LIM_VARIANT_WARP : LIM_VARIANT_CTA;
+  pl.arena_smem.assign(pl.codes.size(), 0);
+  if (variant == LIM_VARIANT_WARP) {
+    pl.warp = 1;
+    pl.block = prm->block_threads > 0 ? prm->block_threads : 256;
+    if (pl.block % 32 || pl.block > 1024) return bad(LIM_E_INVAL, "block_threads must be a multiple of 32, <= 1024");
+    const int teams = pl.block / 32;
+    pl.team_smem = (max_all + 15) & ~size_t(15);
+    pl.smem = pl.team_smem * teams;
+    if (pl.smem > (size_t)ctx->smem_optin)
+      return bad(LIM_E_UNSUPPORTED, "codes too large for one warp per shot; use LIM_VARIANT_CTA");
+    std::fill(pl.arena_smem.begin(), pl.arena_smem.end(), 1u);
+    pl.slot_bytes = 0;
+  } else {
+    pl.warp = 0;
+    pl.block = prm->block_threads > 0 ? prm->block_threads : 512;
+    if (pl.block % 32 || pl.block > 1024) return bad(LIM_E_INVAL, "block_threads must be a multiple of 32, <= 1024");
+    const int target = prm->blocks_per_sm > 0 ? prm->blocks_per_sm : 2;
+    size_t cap = (size_t)ctx->smem_per_sm / target;
+    cap = cap > 2048 ? cap - 2048 : cap;
+    cap = std::min(cap, (size_t)ctx->smem_optin);
+    if (max_bits > cap) return bad(LIM_E_UNSUPPORTED, "bit vectors of a code exceed shared memory");
+    size_t team = max_bits, slot = 0;
+    for (size_t i = 0; i < pl.codes.size(); i++) {
+      if (lay[i].bits_bytes + lay[i].arena_bytes <= cap) {
+        pl.arena_smem[i] = 1;
+        team = std::max(team, lay[i].bits_bytes + lay[i].arena_bytes);
+      } else {
+        slot = std::max(slot, lay[i].arena_bytes);
+      }
+    }
+    pl.team_smem = (team + 15) & ~size_t(15);
+    pl.smem = pl.team_smem;
+    pl.slot_bytes = (slot + 255) & ~size_t(255);
+  }
+  int occ = 0;
+  int st = batch_occupancy(pl.warp, dp.prec, dp.rule, dp.feedback, pl.block, pl.smem, &occ);
+  if (st) return st;
+  if (occ < 1) return bad(LIM_E_UNSUPPORTED, "batch kernel does not fit on an SM with this shape");
+  if (prm->blocks_per_sm > 0) occ = std::min(occ, prm->blocks_per_sm);
+  pl.grid = ctx->num_sms * occ;
+  pl.n_teams = (size_t)pl.grid * (pl.warp ? pl.block / 32 : 1);
+  pl.workspace = kWsHeader + pl.n_teams * pl.slot_bytes;
+  return LIM_OK;
+}
+
+void fill_args(const Plan &pl, const lim_point *pts, uint32_t npts, const lim_params *prm,
+               const DevParams &dp, uint64_t seed, void *ws, LaunchArgs &a) {
+  std::memset(&a, 0, sizeof(a));
+  a.prm = dp;
+  a.prm.seed_lo = (uint32_t)seed;
+  a.prm.seed_hi = (uint32_t)(seed >> 32);
+  a.npts = (int32_t)npts;
+  a.ncodes = (int32_t)pl.codes.size();
+  for (size_t i = 0; i < pl.codes.size(); i++) a.codes[i] = pl.codes[i]->dev;
+  uint64_t item = 0;
+  for (uint32_t i = 0; i < npts; i++) {
+    DevPoint &d = a.pts[i];
+    d.code = pl.code_of_point[i];
+    d.T = pts[i].tick_budget > 0 ? pts[i].tick_budget : prm->tick_budget;
+    d.shots = pts[i].shots;
+    d.shot0 = pts[i].shot0;
+    d.point_id = pts[i].point_id;
+    d.arena_smem = pl.arena_smem[d.code];
+    d.p_thr = prob_threshold(pts[i].p);
+    d.item0 = item;
+    item += pts[i].shots;
+  }
+  a.total_items = item;
+  a.team_smem = (uint32_t)pl.team_smem;
+  a.slot_bytes = (uint32_t)pl.slot_bytes;
+  a.slots = pl.slot_bytes ? (uint8_t *)ws + kWsHeader : nullptr;
+  a.queue = (unsigned long long *)ws;
+}
+
+int upload_code(lim_ctx *ctx, HostCode &hc, lim_code **out) {
+  lim_code *c = new (std::nothrow) lim_code();
+  if (!c) return bad(LIM_E_NOMEM, "host allocation failed");
+  c->ctx = ctx;
+  c->host = std::move(hc);
+  const HostCode &h = c->host;
+  const size_t nw = (h.n + 31) / 32;
+  const size_t words = (h.m + 1) + 3 * (size_t)h.E + (h.n + 1) + (size_t)h.k * nw;
+  DevCode &d = c->dev;
+  d.n = h.n;
+  d.m = h.m;
+  d.E = h.E;
+  d.k = h.k;
+  d.nw = (int32_t)nw;
+  d.mw = (h.m + 31) / 32;
+  d.dc_max = h.dc_max;
+  d.dv_max = h.dv_max;
+  if (ctx->device < 0) {  // host-only context
+    *out = c;
+    return LIM_OK;
+  }
+  cudaError_t err = cudaSetDevice(ctx->device);
+  if (err == cudaSuccess) err = cudaMalloc(&c->dmem, words * 4);
+  if (err != cudaSuccess) {
+    delete c;
+    return cuda_fail(err, "cudaMalloc(code tables)");
+  }
+  std::vector<int32_t> buf;
+  buf.reserve(words);
+  auto put = [&buf](const std::vector<int32_t> &v) {
+    size_t o = buf.size();
+    buf.insert(buf.end(), v.begin(), v.end());
+    return o;
+  };
+  size_t o_cptr = put(h.c_ptr), o_cvar = put(h.c_var), o_vptr = put(h.v_ptr), o_vedge = put(h.v_edge),
+         o_vchk = put(h.v_chk);
+  size_t o_lg = buf.size();
+  for (uint32_t w : h.logicals) buf.push_back((int32_t)w);
+  err = cudaMemcpy(c->dmem, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) {
+    cudaFree(c->dmem);
+    delete c;
+    return cuda_fail(err, "cudaMemcpy(code tables)");
+  }
+  int32_t *base = (int32_t *)c->dmem;
+  d.c_ptr = base + o_cptr;
+  d.c_var = base + o_cvar;
+  d.v_ptr = base + o_vptr;
+  d.v_edge = base + o_vedge;
+  d.v_chk = base + o_vchk;
+  d.logicals = (const uint32_t *)(base + o_lg);
+  *out = c;
+  return LIM_OK;
+}
+
+template <class F>
+int guarded(F &&f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc &) {
+    return bad(LIM_E_NOMEM, "host allocation failed");
+  } catch (...) {
+    return bad(LIM_E_INVAL, "unexpected exception");
+  }
+}
+
+}  // namespace
+}  // namespace lim
+
+using namespace lim;
+
+extern "C" {
+
+const char *lim_last_error(void) { return g_last_error.c_str(); }
+int lim_version(void) { return LIM_VERSION; }
+
+int lim_ctx_create(int device, lim_ctx **out) {
+  if (!out) return bad(LIM_E_INVAL, "null output");
+  if (device < 0) {  // host-only context: codes are built and validated, never uploaded
+    lim_ctx *c = new (std::nothrow) lim_ctx();
+    if (!c) return bad(LIM_E_NOMEM, "host allocation failed");
+    c->device = -1;
+    *out = c;
+    return LIM_OK;
+  }
+  cudaError_t err = cudaSetDevice(device);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaSetDevice");
+  lim_ctx *c = new (std::nothrow) lim_ctx();
+  if (!c) return bad(LIM_E_NOMEM, "host allocation failed");
+  c->device = device;
+  int v = 0;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  c->smem_optin = v;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+  c->smem_per_sm = v;
+  err = cudaGetLastError();
+  if (err != cudaSuccess || c->num_sms <= 0) {
+    delete c;
+    return cuda_fail(err, "cudaDeviceGetAttribute");
+  }
+  *out = c;
+  return LIM_OK;
+}
+
+int lim_ctx_destroy(lim_ctx *ctx) {
+  delete ctx;
+  return LIM_OK;
+}
+
+int lim_code_from_csr(lim_ctx *ctx, int32_t m, int32_t n, const int32_t *hx_ptr, const int32_t *hx_col,
+                      int32_t mz, const int32_t *hz_ptr, const int32_t *hz_col, int32_t k,
+                      const uint32_t *logicals, lim_code **out) {
+  return guarded([&] {
+    if (!ctx || !out) return bad(LIM_E_INVAL, "null argument");
+    HostCode hc;
+    int st = build_from_csr(m, n, hx_ptr, hx_col, mz, hz_ptr, hz_col, k, logicals, hc);
+    return st ? st : upload_code(ctx, hc, out);
+  });
+}
+
+int lim_code_rep(lim_ctx *ctx, int32_t d, int periodic, lim_code **out) {
+  return guarded([&] {
+    if (!ctx || !out) return bad(LIM_E_INVAL, "null argument");
+    HostCode hc;
+    int st = build_rep(d, periodic, hc);
+    return st ? st : upload_code(ctx, hc, out);
+  });
+}
+
+int lim_code_toric2d(lim_ctx *ctx, int32_t L, lim_code **out) {
+  return guarded([&] {
+    if (!ctx || !out) return bad(LIM_E_INVAL, "null argument");
+    HostCode hc;
+    int st = build_toric2d(L, hc);
+    return st ? st : upload_code(ctx, hc, out);
+  });
+}
+
+int lim_code_toric3d(lim_ctx *ctx, int32_t L, int sector, lim_code **out) {
+  return guarded([&] {
+    if (!ctx || !out) return bad(LIM_E_INVAL, "null argument");
+    HostCode hc;
+    int st = build_toric3d(L, sector, hc);
+    return st ? st : upload_code(ctx, hc, out);
+  });
+}
+
+int lim_code_bb(lim_ctx *ctx, int32_t l, int32_t m, const int32_t *a_xy, const int32_t *b_xy,
+                lim_code **out) {
+  return guarded([&] {
+    if (!ctx || !out) return bad(LIM_E_INVAL, "null argument");
+    HostCode hc;
+    int st = build_bb(l, m, a_xy, b_xy, hc);
+    return st ? st : upload_code(ctx, hc, out);
+  });
+}
+
+int lim_code_info(const lim_code *code, lim_info *out) {
+  if (!code || !out) return bad(LIM_E_INVAL, "null argument");
+  const HostCode &h = code->host;
+  out->n = h.n;
+  out->m = h.m;
+  out->E = h.E;
+  out->k = h.k;
+  out->dc_min = h.dc_min;
+  out->dc_max = h.dc_max;
+  out->dv_min = h.dv_min;
+  out->dv_max = h.dv_max;
+  return LIM_OK;
+}
+
+int lim_code_export(const lim_code *code, int32_t *hx_ptr, int32_t *hx_col, uint32_t *logicals) {
+  if (!code) return bad(LIM_E_INVAL, "null code");
+  const HostCode &h = code->host;
+  if (hx_ptr) std::memcpy(hx_ptr, h.c_ptr.data(), h.c_ptr.size() * 4);
+  if (hx_col) std::memcpy(hx_col, h.c_var.data(), h.c_var.size() * 4);
+  if (logicals && !h.logicals.empty()) std::memcpy(logicals, h.logicals.data(), h.logicals.size() * 4);
+  return LIM_OK;
+}
+
+int lim_code_destroy(lim_code *code) {
+  if (!code) return LIM_OK;
+  if (code->dmem) cudaFree(code->dmem);
+  delete code;
+  return LIM_OK;
+}
+
+int lim_sample_noise(lim_code *code, double p, uint64_t seed, uint32_t point_id, uint32_t shot0,
+                     uint32_t nshots, uint32_t *e_bits, uint32_t *s_bits, void *stream) {
+  if (!code || (nshots && (!e_bits || !s_bits))) return bad(LIM_E_INVAL, "null argument");
+  if (!code->dmem) return bad(LIM_E_INVAL, "code of a host-only context");
+  if (!(p >= 0.0 && p <= 1.0)) return bad(LIM_E_INVAL, "p must be in [0,1]");
+  if (point_id >= (1u << 28)) return bad(LIM_E_INVAL, "point_id must be < 2^28");
+  return launch_noise(code->dev, prob_threshold(p), (uint32_t)seed, (uint32_t)(seed >> 32), point_id,
+                      shot0, nshots, e_bits, s_bits, stream);
+}
+
+int lim_params_check(const lim_params *prm) {
+  DevParams dp;
+  return derive(prm, dp);
+}
+
+int lim_workspace_size(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+                       size_t *bytes) {
+  return guarded([&] {
+    if (!bytes) return bad(LIM_E_INVAL, "null output");
+    DevParams dp;
+    int st = derive(prm, dp);
+    if (st) return st;
+    Plan pl;
+    st = make_plan(ctx, pts, npts, prm, dp, pl);
+    if (st) return st;
+    *bytes = pl.workspace;
+    return LIM_OK;
+  });
+}
+
+int lim_final_words(const lim_point *pts, uint32_t npts, int32_t *words) {
+  if (!pts || !words) return bad(LIM_E_INVAL, "null argument");
+  int32_t w = 0;
+  for (uint32_t i = 0; i < npts; i++) {
+    if (!pts[i].code) return bad(LIM_E_INVAL, "point without code");
+    w = std::max(w, pts[i].code->dev.nw);
+  }
+  *words = w;
+  return LIM_OK;
+}
+
+int lim_run_batch(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+                  uint64_t seed, void *workspace, size_t workspace_bytes, lim_shot_record *rec,
+                  uint32_t *e_final, lim_tally *tally, void *stream) {
+  return guarded([&] {
+    if (!tally || !workspace) return bad(LIM_E_INVAL, "null tally or workspace");
+    DevParams dp;
+    int st = derive(prm, dp);
+    if (st) return st;
+    Plan pl;
+    st = make_plan(ctx, pts, npts, prm, dp, pl);
+    if (st) return st;
+    if (workspace_bytes < pl.workspace) return bad(LIM_E_NOMEM, "workspace too small");
+    LaunchArgs a;
+    fill_args(pl, pts, npts, prm, dp, seed, workspace, a);
+    a.rec = rec;
+    a.e_final = e_final;
+    if (e_final) lim_final_words(pts, npts, &a.e_final_words);
+    a.tally = tally;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t err = cudaMemsetAsync(workspace, 0, 256, s);
+    if (err == cudaSuccess) err = cudaMemsetAsync(tally, 0, sizeof(lim_tally) * npts, s);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync");
+    if (a.total_items == 0) return LIM_OK;
+    return launch_batch(a, pl.warp, pl.grid, pl.block, pl.smem, stream);
+  });
+}
+
+int lim_trace(lim_ctx *ctx, const lim_code *code, const lim_params *prm, double p, uint64_t seed,
+              uint32_t point_id, uint32_t shot, int32_t max_ticks, void *workspace,
+              size_t workspace_bytes, uint32_t *e_hist, uint32_t *s_hist, lim_shot_record *rec,
+              void *stream) {
+  return guarded([&] {
+    if (!code || !e_hist || !s_hist || !workspace || max_ticks < 0) return bad(LIM_E_INVAL, "bad argument");
+    DevParams dp;
+    int st = derive(prm, dp);
+    if (st) return st;
+    lim_point pt = {code, p, 1, shot, point_id, 0};
+    if (pt.code->dev.m == 0) return bad(LIM_E_INVAL, "empty code");
+    lim_params one = *prm;
+    Plan pl;
+    st = make_plan(ctx, &pt, 1, &one, dp, pl);
+    if (st) return st;
+    if (workspace_bytes < pl.workspace) return bad(LIM_E_NOMEM, "workspace too small");
+    LaunchArgs a;
+    fill_args(pl, &pt, 1, &one, dp, seed, workspace, a);
+    a.rec = rec;
+    a.tally = (lim_tally *)((uint8_t *)workspace + 256);
+    a.trace_e = e_hist;
+    a.trace_s = s_hist;
+    a.trace_ticks = std::min(max_ticks, a.pts[0].T);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t err = cudaMemsetAsync(workspace, 0, kWsHeader, s);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync");
+    // rows beyond the budget are never written by the kernel: clear them
+    const int T = a.pts[0].T;
+    if (max_ticks > T) {
+      err = cudaMemsetAsync(e_hist + (size_t)(T + 1) * code->dev.nw, 0,
+                            (size_t)(max_ticks - T) * code->dev.nw * 4, s);
+      if (err == cudaSuccess)
+        err = cudaMemsetAsync(s_hist + (size_t)(T + 1) * code->dev.mw, 0,
+                              (size_t)(max_ticks - T) * code->dev.mw * 4, s);
+      if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync");
+    }
+    return launch_batch(a, pl.warp, pl.grid, pl.block, pl.smem, stream);
+  });
+}
+
+int lim_bp_sweeps(const lim_code *code, const lim_params *prm, uint32_t nstates, const uint8_t *s,
+                  const void *cv_in, const void *vc_in, void *cv_out, void *vc_out, int32_t ksweeps,
+                  void *scratch, size_t scratch_bytes, void *stream) {
+  return guarded([&] {
+    if (!code || (nstates && (!s || !cv_in || !vc_in || !cv_out || !vc_out)))
+      return bad(LIM_E_INVAL, "null argument");
+    if (ksweeps < 1) return bad(LIM_E_INVAL, "ksweeps must be >= 1");
+    if (!code->dmem) return bad(LIM_E_INVAL, "code of a host-only context");
+    if (cv_out == cv_in || vc_out == vc_in || cv_out == vc_in || vc_out == cv_in)
+      return bad(LIM_E_INVAL, "outputs must not alias inputs");
+    DevParams dp;
+    int st = derive(prm, dp);
+    if (st) return st;
+    const size_t slab = (size_t)nstates * code->dev.E * msg_bytes(dp.prec);
+    if (ksweeps > 1 && (!scratch || scratch_bytes < 4 * slab))
+      return bad(LIM_E_NOMEM, "scratch must hold 4 * nstates * E messages for ksweeps > 1");
+    const void *ci = cv_in, *vi = vc_in;
+    for (int k = 0; k < ksweeps; k++) {
+      void *co, *vo;
+      if (k == ksweeps - 1) {
+        co = cv_out;
+        vo = vc_out;
+      } else {
+        uint8_t *base = (uint8_t *)scratch + (k & 1) * 2 * slab;
+        co = base;
+        vo = base + slab;
+      }
+      st = launch_bp_sweep(code->dev, dp, nstates, s, ci, vi, co, vo, stream);
+      if (st) return st;
+      ci = co;
+      vi = vo;
+    }
+    return LIM_OK;
+  });
+}
+
+int lim_readout(const lim_code *code, const lim_params *prm, uint32_t nstates, const void *cv, float *L,
+                void *stream) {
+  if (!code || (nstates && (!cv || !L))) return bad(LIM_E_INVAL, "null argument");
+  if (!code->dmem) return bad(LIM_E_INVAL, "code of a host-only context");
+  DevParams dp;
+  int st = derive(prm, dp);
+  if (st) return st;
+  return launch_readout(code->dev, dp, nstates, cv, L, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// lim_internal.h -- structures shared by the host side and the kernels of the
+// library (not part of the C ABI).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lim.h"
+
+#ifdef __CUDACC__
+#define LIM_HD __host__ __device__
+#else
+#define LIM_HD
+#endif
+
+namespace lim {
+
+constexpr int kMaxDeg = LIM_MAX_DEGREE;
+
+LIM_HD inline size_t msg_bytes_dev(int prec) {
+  return prec == LIM_PREC_F32 ? 4 : (prec == LIM_PREC_I8 ? 1 : 2);
+}
+
+// Device view of a code: CSR (check -> qubit, edge id = CSR position) and CSC
+// (qubit -> (edge, check), ascending check) tables in device memory.
+struct DevCode {
+  int32_t n, m, E, k;
+  int32_t nw, mw;              // words of the bit vectors e and s
+  int32_t dc_max, dv_max;
+  const int32_t *c_ptr;        // [m+1]
+  const int32_t *c_var;        // [E]
+  const int32_t *v_ptr;        // [n+1]
+  const int32_t *v_edge;       // [E]
+  const int32_t *v_chk;        // [E]
+  const uint32_t *logicals;    // [k*nw]
+};
+
+struct DevPoint {
+  int32_t code;        // index into LaunchArgs::codes
+  int32_t T;           // tick budget
+  uint32_t shots;
+  uint32_t shot0;
+  uint32_t point_id;
+  uint32_t arena_smem; // 1: message arena of this code lives in shared memory
+  uint64_t p_thr;      // floor(p * 2^32), 2^32 for p >= 1
+  uint64_t item0;      // first work item of this point
+};
+
+// Scalars of the method in the working arithmetic (binary32 or int32 steps).
+struct DevParams {
+  int32_t rule, feedback, prec, K, gauge_on_move;
+  int32_t alpha_is_one;
+  float pi_f, clamp_f, alpha_f;
+  int32_t pi_q, clamp_q, A;
+  float theta_f[kMaxDeg + 1];    // evidence threshold by check degree
+  int32_t theta_q[kMaxDeg + 1];
+  uint64_t ring_thr;             // floor(rho * 2^32)
+  uint32_t seed_lo, seed_hi;
+};
+
+// Everything a persistent launch needs, passed by value as a kernel parameter.
+struct LaunchArgs {
+  DevParams prm;
+  int32_t npts, ncodes;
+  uint64_t total_items;
+  uint32_t team_smem;      // bytes of dynamic shared memory per team
+  uint32_t slot_bytes;     // bytes of one global arena slot
+  uint8_t *slots;          // [n_teams * slot_bytes] global arenas
+  unsigned long long *queue;  // work-queue counter
+  lim_shot_record *rec;    // nullable
+  uint32_t *e_final;       // nullable
+  int32_t e_final_words;
+  lim_tally *tally;        // [npts]
+  // trace of one item (lim_trace)
+  uint32_t *trace_e, *trace_s;
+  int32_t trace_ticks;
+  DevCode codes[LIM_MAX_CODES];
+  DevPoint pts[LIM_MAX_POINTS];
+};
+
+// Per-code sizes used to lay out team memory.
+struct CodeLayout {
+  size_t bits_bytes;   // e, s, s0, sigma bit vectors (always shared memory)
+  size_t arena_bytes;  // messages + per-check feedback scratch
+};
+
+size_t msg_bytes(int prec);
+CodeLayout code_layout(const DevCode &c, int prec);
+
+// Host-side code object.
+struct HostCode {
+  int32_t n = 0, m = 0, E = 0, k = 0;
+  std::vector<int32_t> c_ptr, c_var, v_ptr, v_edge, v_chk;
+  std::vector<uint32_t> logicals;
+  int32_t dc_min = 0, dc_max = 0, dv_min = 0, dv_max = 0;
+};
+
+// Builders (host): validate, derive CSC, logicals.  Return a LIM_* status and
+// set the error text.
+int build_from_csr(int32_t m, int32_t n, const int32_t *hx_ptr, const int32_t *hx_col, int32_t mz,
+                   const int32_t *hz_ptr, const int32_t *hz_col, int32_t k,
+                   const uint32_t *logicals, HostCode &out);
+int build_rep(int32_t d, int periodic, HostCode &out);
+int build_toric2d(int32_t L, HostCode &out);
+int build_toric3d(int32_t L, int sector, HostCode &out);
+int build_bb(int32_t l, int32_t m, const int32_t *a_xy, const int32_t *b_xy, HostCode &out);
+
+void set_error(const std::string &msg);
+
+// Kernel launchers (lim_kernels.cu).
+int launch_batch(const LaunchArgs &args, int variant_warp, int grid, int block, size_t smem,
+                 void *stream);
+int batch_occupancy(int warp, int prec, int rule, int fb, int block, size_t smem,
+                    int *blocks_per_sm);
+int launch_noise(const DevCode &c, uint64_t p_thr, uint32_t seed_lo, uint32_t seed_hi,
+                 uint32_t point_id, uint32_t shot0, uint32_t nshots, uint32_t *e_bits,
+                 uint32_t *s_bits, void *stream);
+int launch_bp_sweep(const DevCode &c, const DevParams &p, uint32_t nstates, const uint8_t *s,
+                    const void *cv_in, const void *vc_in, void *cv_out, void *vc_out,
+                    void *stream);
+int launch_readout(const DevCode &c, const DevParams &p, uint32_t nstates, const void *cv,
+                   float *L, void *stream);
+
+}  // namespace lim

@@ -1,0 +1,378 @@
+"""Python binding of the C ABI in ``include/lim.h`` (ctypes).
+
+Argument marshalling only: every step of the inference machine runs in the
+CUDA library ``liblim.so``.  PyTorch provides device memory (workspace, output
+buffers) and streams.  If the library is missing, importing this module fails
+loudly: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblim.so")
+
+LIM_OK = 0
+STATUS = {0: "LIM_OK", 1: "LIM_E_INVAL", 2: "LIM_E_NOMEM", 3: "LIM_E_CUDA", 4: "LIM_E_TIMEOUT",
+          5: "LIM_E_NOT_CSS", 6: "LIM_E_UNSUPPORTED"}
+RULE = {"minsum": 0, "sumproduct": 1}
+FEEDBACK = {"check_move": 0, "bit_discrete": 1}
+PREC = {"f32": 1, "f16": 2, "bf16": 3, "i16": 4, "i8": 5}
+VARIANT = {"auto": 0, "cta": 1, "warp": 2, "plain": 3}
+SECTOR = {"point": 0, "membrane": 1}
+MSG_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "i16": 2, "i8": 1}
+HIST_BINS = 24
+MAX_POINTS = 128
+
+# Every extern "C" symbol declared in include/lim.h.
+EXPORTS = ["lim_last_error", "lim_version", "lim_ctx_create", "lim_ctx_destroy", "lim_code_from_csr",
+           "lim_code_rep", "lim_code_toric2d", "lim_code_toric3d", "lim_code_bb", "lim_code_info",
+           "lim_code_export", "lim_code_destroy", "lim_sample_noise", "lim_params_check",
+           "lim_workspace_size", "lim_run_batch", "lim_final_words", "lim_trace", "lim_bp_sweeps",
+           "lim_readout"]
+
+
+class LimError(RuntimeError):
+    pass
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("E", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("dc_min", ctypes.c_int32), ("dc_max", ctypes.c_int32),
+                ("dv_min", ctypes.c_int32), ("dv_max", ctypes.c_int32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("rule", ctypes.c_int32), ("feedback", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("quant_scale", ctypes.c_double),
+                ("q", ctypes.c_double), ("clamp", ctypes.c_double), ("tau", ctypes.c_double),
+                ("dt_tick", ctypes.c_double), ("sweeps_per_tick", ctypes.c_int32),
+                ("ring_prob", ctypes.c_double), ("tick_budget", ctypes.c_int32),
+                ("gauge_on_move", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
+class Point(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_void_p), ("p", ctypes.c_double), ("shots", ctypes.c_uint32),
+                ("shot0", ctypes.c_uint32), ("point_id", ctypes.c_uint32),
+                ("tick_budget", ctypes.c_int32)]
+
+
+RECORD_DTYPE = np.dtype([("t_clr", np.int32), ("converged", np.int32), ("failed", np.int32),
+                         ("moves", np.int32), ("ticks", np.int64), ("sweeps", np.int64)])
+TALLY_FIELDS = ["shots", "failures", "nonconverged", "sum_t", "sum_t2", "moves", "ticks", "sweeps",
+                "msg_updates", "errors"]
+TALLY_DTYPE = np.dtype([(f, np.int64) for f in TALLY_FIELDS] + [("hist", np.int64, (HIST_BINS,))])
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise LimError(f"{LIB_PATH} is missing: build it with `python -m paper_2609_38139_b300.build` "
+                       "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, u32, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    L.lim_last_error.restype = ctypes.c_char_p
+    L.lim_ctx_create.argtypes = [ctypes.c_int, pp]
+    L.lim_ctx_destroy.argtypes = [vp]
+    L.lim_code_from_csr.argtypes = [vp, i32, i32, vp, vp, i32, vp, vp, i32, vp, pp]
+    L.lim_code_rep.argtypes = [vp, i32, ctypes.c_int, pp]
+    L.lim_code_toric2d.argtypes = [vp, i32, pp]
+    L.lim_code_toric3d.argtypes = [vp, i32, ctypes.c_int, pp]
+    L.lim_code_bb.argtypes = [vp, i32, i32, vp, vp, pp]
+    L.lim_code_info.argtypes = [vp, ctypes.POINTER(Info)]
+    L.lim_code_export.argtypes = [vp, vp, vp, vp]
+    L.lim_code_destroy.argtypes = [vp]
+    L.lim_sample_noise.argtypes = [vp, dbl, u64, u32, u32, u32, vp, vp, vp]
+    L.lim_params_check.argtypes = [ctypes.POINTER(Params)]
+    L.lim_workspace_size.argtypes = [vp, vp, u32, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]
+    L.lim_run_batch.argtypes = [vp, vp, u32, ctypes.POINTER(Params), u64, vp, ctypes.c_size_t, vp, vp,
+                                vp, vp]
+    L.lim_final_words.argtypes = [vp, u32, ctypes.POINTER(i32)]
+    L.lim_trace.argtypes = [vp, vp, ctypes.POINTER(Params), dbl, u64, u32, u32, i32, vp,
+                            ctypes.c_size_t, vp, vp, vp, vp]
+    L.lim_bp_sweeps.argtypes = [vp, ctypes.POINTER(Params), u32, vp, vp, vp, vp, vp, i32, vp,
+                                ctypes.c_size_t, vp]
+    L.lim_readout.argtypes = [vp, ctypes.POINTER(Params), u32, vp, vp, vp]
+    _lib = L
+    return L
+
+
+def check(st: int, what: str = "") -> None:
+    if st != LIM_OK:
+        msg = lib().lim_last_error().decode(errors="replace")
+        raise LimError(f"{what}: {STATUS.get(st, st)}: {msg}")
+
+
+def params(rule="minsum", feedback="check_move", precision="f32", quant_scale=2.0 ** -6, q=0.05,
+           clamp=1000.0, tau=0.1, dt_tick=0.1, sweeps_per_tick=1, ring_prob=-1.0, tick_budget=32,
+           gauge_on_move=0, variant="auto", block_threads=0, blocks_per_sm=0) -> Params:
+    return Params(RULE[rule], FEEDBACK[feedback], PREC[precision], float(quant_scale), float(q),
+                  float(clamp), float(tau), float(dt_tick), int(sweeps_per_tick), float(ring_prob),
+                  int(tick_budget), int(gauge_on_move), VARIANT[variant], int(block_threads),
+                  int(blocks_per_sm))
+
+
+def prec_name(prm: Params) -> str:
+    return {v: k for k, v in PREC.items()}[prm.precision]
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Context:
+    """A library context on one CUDA device (``device < 0``: host-only)."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        h = ctypes.c_void_p()
+        check(lib().lim_ctx_create(device, ctypes.byref(h)), "lim_ctx_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib().lim_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- codes ------------------------------------------------------------
+    def _code(self, fn, *args, name=""):
+        h = ctypes.c_void_p()
+        check(fn(self.handle, *args, ctypes.byref(h)), fn.__name__)
+        return Code(self, h, name)
+
+    def rep(self, d: int, periodic: bool = False) -> "Code":
+        return self._code(lib().lim_code_rep, int(d), int(periodic), name=f"rep_{d}")
+
+    def toric2d(self, L: int) -> "Code":
+        return self._code(lib().lim_code_toric2d, int(L), name=f"toric2d_{L}")
+
+    def toric3d(self, L: int, sector: str = "point") -> "Code":
+        return self._code(lib().lim_code_toric3d, int(L), SECTOR[sector], name=f"toric3d_{sector}_{L}")
+
+    def bb(self, l: int, m: int, a_xy=None, b_xy=None) -> "Code":
+        a = None if a_xy is None else np.ascontiguousarray(np.asarray(a_xy, np.int32).ravel())
+        b = None if b_xy is None else np.ascontiguousarray(np.asarray(b_xy, np.int32).ravel())
+        return self._code(lib().lim_code_bb, int(l), int(m),
+                          None if a is None else a.ctypes.data, None if b is None else b.ctypes.data,
+                          name=f"bb_{l}_{m}")
+
+    def from_csr(self, n: int, hx_ptr, hx_col, hz_ptr=None, hz_col=None, logicals_packed=None,
+                 name="csr") -> "Code":
+        hp = np.ascontiguousarray(hx_ptr, np.int32)
+        hc = np.ascontiguousarray(hx_col, np.int32)
+        m = len(hp) - 1
+        zp = None if hz_ptr is None else np.ascontiguousarray(hz_ptr, np.int32)
+        zc = None if hz_col is None else np.ascontiguousarray(hz_col, np.int32)
+        mz = 0 if zp is None else len(zp) - 1
+        lg = None if logicals_packed is None else np.ascontiguousarray(logicals_packed, np.uint32)
+        k = 0 if lg is None else lg.shape[0]
+        return self._code(lib().lim_code_from_csr, m, int(n), hp.ctypes.data, hc.ctypes.data, mz,
+                          None if zp is None else zp.ctypes.data, None if zc is None else zc.ctypes.data,
+                          k, None if lg is None else lg.ctypes.data, name=name)
+
+    def from_inputs(self, code) -> "Code":
+        """A library code from an ``inputs.Code`` (same CSR and logicals)."""
+        return self.from_csr(code.n, code.hx_ptr, code.hx_col, logicals_packed=code.logicals_packed(),
+                             name=code.name)
+
+
+class Code:
+    def __init__(self, ctx: Context, handle, name=""):
+        self.ctx = ctx
+        self.handle = handle
+        self.name = name
+        inf = Info()
+        check(lib().lim_code_info(handle, ctypes.byref(inf)), "lim_code_info")
+        self.info = inf
+        self.n, self.m, self.E, self.k = inf.n, inf.m, inf.E, inf.k
+        self.nw = (self.n + 31) // 32
+        self.mw = (self.m + 31) // 32
+
+    def export(self):
+        hp = np.zeros(self.m + 1, np.int32)
+        hc = np.zeros(max(self.E, 1), np.int32)
+        lg = np.zeros((max(self.k, 1), self.nw), np.uint32)
+        check(lib().lim_code_export(self.handle, hp.ctypes.data, hc.ctypes.data, lg.ctypes.data),
+              "lim_code_export")
+        return hp, hc[:self.E], lg[:self.k]
+
+    def close(self):
+        if self.handle:
+            lib().lim_code_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def params_check(prm: Params) -> None:
+    check(lib().lim_params_check(ctypes.byref(prm)), "lim_params_check")
+
+
+def _points(points) -> "ctypes.Array":
+    """``points``: list of (Code, p, shots, shot0, point_id[, tick_budget])."""
+    arr = (Point * len(points))()
+    for i, pt in enumerate(points):
+        code, p, shots, shot0, pid = pt[:5]
+        tb = pt[5] if len(pt) > 5 else 0
+        arr[i] = Point(code.handle.value, float(p), int(shots), int(shot0), int(pid), int(tb))
+    return arr
+
+
+def workspace_size(ctx: Context, points, prm: Params) -> int:
+    pts = _points(points)
+    out = ctypes.c_size_t()
+    check(lib().lim_workspace_size(ctx.handle, pts, len(points), ctypes.byref(prm), ctypes.byref(out)),
+          "lim_workspace_size")
+    return int(out.value)
+
+
+def final_words(points) -> int:
+    pts = _points(points)
+    w = ctypes.c_int32()
+    check(lib().lim_final_words(pts, len(points), ctypes.byref(w)), "lim_final_words")
+    return int(w.value)
+
+
+class Batch:
+    """Device buffers of one ``lim_run_batch`` configuration, reusable across calls."""
+
+    def __init__(self, ctx: Context, points, prm: Params, records: bool = True,
+                 e_final: bool = False):
+        import torch
+        self.ctx, self.points, self.prm = ctx, list(points), prm
+        self.pts = _points(self.points)
+        self.nshots = sum(int(p[2]) for p in self.points)
+        dev = torch.device("cuda", ctx.device)
+        self.ws_bytes = workspace_size(ctx, self.points, prm)
+        self.ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=dev)
+        self.tally = torch.zeros(len(self.points) * TALLY_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        self.rec = (torch.empty(max(self.nshots, 1) * RECORD_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+                    if records else None)
+        self.words = final_words(self.points) if e_final else 0
+        self.e_final = (torch.empty(max(self.nshots * self.words, 1), dtype=torch.int32, device=dev)
+                        if e_final else None)
+
+    def run(self, seed: int, stream=None) -> None:
+        st = _stream_ptr(stream)
+        check(lib().lim_run_batch(self.ctx.handle, self.pts, len(self.points), ctypes.byref(self.prm),
+                                  int(seed), self.ws.data_ptr(), self.ws_bytes,
+                                  None if self.rec is None else self.rec.data_ptr(),
+                                  None if self.e_final is None else self.e_final.data_ptr(),
+                                  self.tally.data_ptr(), st), "lim_run_batch")
+
+    def tallies(self) -> np.ndarray:
+        return np.frombuffer(self.tally.cpu().numpy().tobytes(), dtype=TALLY_DTYPE).copy()
+
+    def records(self) -> np.ndarray:
+        raw = self.rec.cpu().numpy().tobytes()[:self.nshots * RECORD_DTYPE.itemsize]
+        return np.frombuffer(raw, dtype=RECORD_DTYPE).copy()
+
+    def finals(self) -> np.ndarray:
+        a = self.e_final.cpu().numpy().view(np.uint32)[:self.nshots * self.words]
+        return a.reshape(self.nshots, self.words).copy()
+
+
+def run_batch(ctx: Context, points, prm: Params, seed: int, e_final: bool = False):
+    """Run once and return (tallies, records[, finals]) on the host (synchronises)."""
+    import torch
+    b = Batch(ctx, points, prm, records=True, e_final=e_final)
+    b.run(seed)
+    torch.cuda.synchronize(ctx.device)
+    out = (b.tallies(), b.records())
+    return out + ((b.finals(),) if e_final else ())
+
+
+def sample_noise(code: Code, p: float, seed: int, point_id: int, shot0: int, nshots: int, stream=None):
+    import torch
+    dev = torch.device("cuda", code.ctx.device)
+    e = torch.empty(max(nshots * code.nw, 1), dtype=torch.int32, device=dev)
+    s = torch.empty(max(nshots * code.mw, 1), dtype=torch.int32, device=dev)
+    check(lib().lim_sample_noise(code.handle, float(p), int(seed), int(point_id), int(shot0), int(nshots),
+                                 e.data_ptr(), s.data_ptr(), _stream_ptr(stream)), "lim_sample_noise")
+    return e[:nshots * code.nw].view(nshots, code.nw), s[:nshots * code.mw].view(nshots, code.mw)
+
+
+def trace(ctx: Context, code: Code, prm: Params, p: float, seed: int, point_id: int, shot: int,
+          max_ticks: int):
+    """(e_hist [T+1, nw], s_hist [T+1, mw], record) of one shot, on the host."""
+    import torch
+    dev = torch.device("cuda", ctx.device)
+    ws_bytes = workspace_size(ctx, [(code, p, 1, shot, point_id)], prm)
+    ws = torch.empty(max(ws_bytes, 4096), dtype=torch.uint8, device=dev)
+    eh = torch.zeros((max_ticks + 1) * code.nw, dtype=torch.int32, device=dev)
+    sh = torch.zeros((max_ticks + 1) * code.mw, dtype=torch.int32, device=dev)
+    rec = torch.zeros(RECORD_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    check(lib().lim_trace(ctx.handle, code.handle, ctypes.byref(prm), float(p), int(seed), int(point_id),
+                          int(shot), int(max_ticks), ws.data_ptr(), ws.numel(), eh.data_ptr(), sh.data_ptr(),
+                          rec.data_ptr(), _stream_ptr(None)), "lim_trace")
+    torch.cuda.synchronize(ctx.device)
+    r = np.frombuffer(rec.cpu().numpy().tobytes(), dtype=RECORD_DTYPE)[0]
+    return (eh.cpu().numpy().view(np.uint32).reshape(max_ticks + 1, code.nw),
+            sh.cpu().numpy().view(np.uint32).reshape(max_ticks + 1, code.mw), r)
+
+
+_TORCH_DT = {"f32": "float32", "f16": "float16", "bf16": "bfloat16", "i16": "int16", "i8": "int8"}
+
+
+def torch_msg_dtype(prm: Params):
+    import torch
+    return getattr(torch, _TORCH_DT[prec_name(prm)])
+
+
+def bp_sweeps(code: Code, prm: Params, s, cv, vc, ksweeps: int = 1, stream=None):
+    """K Jacobi sweeps on fixed states.  ``s`` uint8 [B, m]; ``cv``, ``vc`` [B, E]
+    device tensors in the storage dtype of ``prm``.  Returns (cv_out, vc_out)."""
+    import torch
+    B = s.shape[0]
+    cvo = torch.empty_like(cv)
+    vco = torch.empty_like(vc)
+    scratch = None
+    sb = 0
+    if ksweeps > 1:
+        scratch = torch.empty(4 * cv.numel() * cv.element_size(), dtype=torch.uint8, device=cv.device)
+        sb = scratch.numel()
+    check(lib().lim_bp_sweeps(code.handle, ctypes.byref(prm), B, s.data_ptr(), cv.data_ptr(), vc.data_ptr(),
+                              cvo.data_ptr(), vco.data_ptr(), int(ksweeps),
+                              None if scratch is None else scratch.data_ptr(), sb, _stream_ptr(stream)),
+          "lim_bp_sweeps")
+    return cvo, vco
+
+
+def readout(code: Code, prm: Params, cv, stream=None):
+    import torch
+    B = cv.shape[0]
+    L = torch.empty((B, code.n), dtype=torch.float32, device=cv.device)
+    check(lib().lim_readout(code.handle, ctypes.byref(prm), B, cv.data_ptr(), L.data_ptr(),
+                            _stream_ptr(stream)), "lim_readout")
+    return L
+
+
+def bits_to_bytes(words: np.ndarray, nbits: int) -> np.ndarray:
+    """Unpack little-endian 32-bit words into a 0/1 byte array of length nbits (last axis)."""
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    b = np.unpackbits(w.view(np.uint8), axis=-1, bitorder="little")
+    return b[..., :nbits]

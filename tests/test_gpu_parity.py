@@ -1,0 +1,311 @@
+"""GPU parity: the CUDA path against the oracle, shot by shot, through the C ABI.
+
+Bars (derived from the arithmetic; see the design notes):
+  * integer, bit and index results (noise, syndromes, t_clr, flags, moves,
+    final residuals, integer messages) are bit-exact;
+  * floating min-sum messages are bit-exact against the oracle's emulation of
+    the same precision (binary32 ops in the same order, same storage rounding),
+    and within |m32 - m64| <= 1e-5 max(1, |m64|) of the FP64 oracle;
+  * sum-product messages (transcendentals) are within that tolerance of FP64;
+  * logical error rates agree with the FP64 oracle within 3 sigma (paired test).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2609_38139_b300 import inputs as I
+
+from parity import compare_records, oracle_params, oracle_point, paired_ok
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_38139_b300 import build, lim
+    build.build()
+    return lim
+
+
+@pytest.fixture(scope="module")
+def ctx(L):
+    return L.Context(0)
+
+
+def _unpack(words, nbits):
+    from paper_2609_38139_b300.lim import bits_to_bytes
+    return bits_to_bytes(np.asarray(words).view(np.uint32), nbits)
+
+
+# ---------------------------------------------------------------------------
+# noise
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("maker", [lambda: I.toric2d(8), lambda: I.toric2d(5), lambda: I.rep_code(2000),
+                                   lambda: I.bb_code(12, 6), lambda: I.toric3d_membrane(3)])
+@pytest.mark.parametrize("p", [0.0, 0.05, 0.45, 1.0])
+def test_noise_bit_exact(L, ctx, maker, p):
+    code = maker()
+    lc = ctx.from_inputs(code)
+    e, s = L.sample_noise(lc, p, 77, 3, 5, 40)
+    torch.cuda.synchronize()
+    e = _unpack(e.cpu().numpy(), code.n)
+    s = _unpack(s.cpu().numpy(), code.m)
+    oc = O.OracleCode.from_code(code)
+    for i in range(40):
+        eo, so = O.noise(oc, p, 77, 3, 5 + i)
+        assert np.array_equal(e[i], eo), i
+        assert np.array_equal(s[i], so), i
+
+
+# ---------------------------------------------------------------------------
+# fixed-state sweeps and read-out
+# ---------------------------------------------------------------------------
+def _random_state(rng, code, prec, B, scale):
+    if prec in ("i16", "i8"):
+        q = 3000 if prec == "i16" else 120
+        cv = rng.integers(-q, q + 1, (B, code.E)).astype(np.float64)
+        vc = rng.integers(-q, q + 1, (B, code.E)).astype(np.float64)
+    else:
+        cv = rng.normal(0, scale, (B, code.E))
+        vc = rng.normal(0, scale, (B, code.E))
+        cv[:, ::7] = 0.0
+        cv, vc = np.float32(cv).astype(np.float64), np.float32(vc).astype(np.float64)
+        if prec == "f16":
+            cv, vc = np.float16(cv).astype(np.float64), np.float16(vc).astype(np.float64)
+        if prec == "bf16":
+            cv = torch.from_numpy(cv).to(torch.bfloat16).double().numpy()
+            vc = torch.from_numpy(vc).to(torch.bfloat16).double().numpy()
+    s = rng.integers(0, 2, (B, code.m)).astype(np.uint8)
+    return s, cv, vc
+
+
+def _to_dev(L, prm, a):
+    return torch.from_numpy(a).to(L.torch_msg_dtype(prm)).cuda()
+
+
+CODES = {"toric2d_6": lambda: I.toric2d(6), "bb_6_6": lambda: I.bb_code(6, 6),
+         "membrane_3": lambda: I.toric3d_membrane(3), "repP_9": lambda: I.rep_code(9, True),
+         "point_3": lambda: I.toric3d_point(3)}
+
+
+@pytest.mark.parametrize("cname", list(CODES))
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16", "i16", "i8"])
+@pytest.mark.parametrize("relaxed", [False, True])
+def test_minsum_sweeps_bit_exact(L, ctx, cname, prec, relaxed):
+    code = CODES[cname]()
+    lc = ctx.from_inputs(code)
+    prm = L.params(precision=prec, quant_scale=2 ** -6 if prec == "i16" else 0.25, clamp=40.0,
+                   tau=0.1, dt_tick=0.03 if relaxed else 0.1)
+    rng = np.random.default_rng(hash((cname, prec)) % 2 ** 32)
+    B, K = 6, 3
+    s, cv, vc = _random_state(rng, code, prec, B, 15.0)
+    cvo, vco = L.bp_sweeps(lc, prm, torch.from_numpy(s).cuda(), _to_dev(L, prm, cv), _to_dev(L, prm, vc), K)
+    cvo = cvo.double().cpu().numpy()
+    vco = vco.double().cpu().numpy()
+    Lg = L.readout(lc, prm, _to_dev(L, prm, cv)).double().cpu().numpy()
+    oc = O.OracleCode.from_code(code)
+    op = oracle_params(prm)
+    for b in range(B):
+        rc, rv = O.bp_sweeps(oc, op, s[b], cv[b], vc[b], K)
+        assert np.array_equal(cvo[b], rc), (b, np.max(np.abs(cvo[b] - rc)))
+        assert np.array_equal(vco[b], rv), (b, np.max(np.abs(vco[b] - rv)))
+        assert np.array_equal(Lg[b], O.readout(oc, op, cv[b])), b
+
+
+@pytest.mark.parametrize("cname", ["toric2d_6", "bb_6_6", "membrane_3"])
+@pytest.mark.parametrize("rule", ["minsum", "sumproduct"])
+def test_f32_sweeps_match_fp64_oracle(L, ctx, cname, rule):
+    """The 1e-5 relative bar against FP64 messages, on fixed states."""
+    code = CODES[cname]()
+    lc = ctx.from_inputs(code)
+    prm = L.params(precision="f32", rule=rule)
+    rng = np.random.default_rng(5)
+    B = 8
+    s, cv, vc = _random_state(rng, code, "f32", B, 6.0)
+    cvo, vco = L.bp_sweeps(lc, prm, torch.from_numpy(s).cuda(), _to_dev(L, prm, cv), _to_dev(L, prm, vc), 1)
+    cvo = cvo.double().cpu().numpy()
+    vco = vco.double().cpu().numpy()
+    oc = O.OracleCode.from_code(code)
+    op = oracle_params(prm, precision="f64")
+    for b in range(B):
+        rc, rv = O.bp_sweeps(oc, op, s[b], cv[b], vc[b], 1)
+        assert np.all(np.abs(cvo[b] - rc) <= 1e-5 * np.maximum(1.0, np.abs(rc))), b
+        assert np.all(np.abs(vco[b] - rv) <= 1e-5 * np.maximum(1.0, np.abs(rv))), b
+
+
+# ---------------------------------------------------------------------------
+# whole trajectories, shot by shot
+# ---------------------------------------------------------------------------
+def _batch_vs_oracle(L, ctx, code, prm, p, nshots, seed=11, point_id=2, shot0=0, finals=True):
+    lc = ctx.from_inputs(code)
+    tal, rec, fin = L.run_batch(ctx, [(lc, p, nshots, shot0, point_id)], prm, seed, e_final=True)
+    ora = oracle_point(code, prm, p, seed, point_id, shot0, nshots)
+    compare_records(rec, ora, f"{code.name} {L.prec_name(prm)}")
+    assert tal[0]["shots"] == nshots and tal[0]["errors"] == 0
+    assert tal[0]["failures"] == int(ora["failed"].sum())
+    assert tal[0]["nonconverged"] == int((ora["converged"] == 0).sum())
+    assert tal[0]["sweeps"] == int(ora["sweeps"].sum())
+    if finals:
+        # residual of each shot = e0 + correction; check it through the syndrome-free
+        # failure test and, on a sample, against the oracle's final state
+        oc = O.OracleCode.from_code(code)
+        op = oracle_params(prm)
+        e_gpu = _unpack(fin, code.n)
+        for sh in range(0, nshots, max(1, nshots // 16)):
+            r = O.run_shot(oc, op, p, seed, point_id, shot0 + sh, trace_ticks=0)
+            assert r["ticks"] == rec[sh]["ticks"]
+            e_or = _final_e(oc, op, p, seed, point_id, shot0 + sh)
+            assert np.array_equal(e_gpu[sh], e_or), sh
+    return tal, rec
+
+
+def _final_e(oc, op, p, seed, pid, shot):
+    T = op.tick_budget
+    r = O.run_shot(oc, op, p, seed, pid, shot, trace_ticks=T)
+    return r["trace"]["e_hist"][T]
+
+
+@pytest.mark.parametrize("variant", ["cta", "warp"])
+def test_toric2d_L8_config_f32(L, ctx, variant):
+    """2D toric code L=8, p=0.05, FP32 min-sum, 1 sweep per tick, budget 4L, 1000 shots."""
+    prm = L.params(precision="f32", tick_budget=32, variant=variant)
+    _batch_vs_oracle(L, ctx, I.toric2d(8), prm, 0.05, 1000)
+
+
+@pytest.mark.parametrize("prec", ["f32", "i16"])
+def test_rep_chain_2000_discrete(L, ctx, prec):
+    """Open repetition chain d=2000, p=0.45, bit-centric machine (BP exact on the chain)."""
+    prm = L.params(feedback="bit_discrete", precision=prec, quant_scale=2 ** -6, tick_budget=8001,
+                   variant="cta")
+    tal, rec = _batch_vs_oracle(L, ctx, I.rep_code(2000), prm, 0.45, 96, finals=False)
+    # Theorem (rep code): failure iff the initial error has a majority
+    oc = O.OracleCode.from_code(I.rep_code(2000))
+    for sh in range(96):
+        e0, _ = O.noise(oc, 0.45, 11, 2, sh)
+        w = int(e0.sum())
+        if 2 * w != 2000:
+            assert rec[sh]["failed"] == int(2 * w > 2000)
+
+
+@pytest.mark.parametrize("maker,prec,qs,variant", [
+    (lambda: I.toric3d_membrane(4), "i16", 2 ** -6, "cta"),
+    (lambda: I.toric3d_membrane(3), "i16", 2 ** -6, "warp"),
+    (lambda: I.bb_code(6, 6), "i8", 0.25, "warp"),
+    (lambda: I.bb_code(12, 6), "i8", 0.25, "cta"),
+    (lambda: I.toric3d_point(4), "f16", 0, "cta"),
+    (lambda: I.toric3d_point(4), "bf16", 0, "warp"),
+    (lambda: I.toric2d(5), "f32", 0, "warp"),
+])
+def test_precisions_bit_exact(L, ctx, maker, prec, qs, variant):
+    code = maker()
+    q = 0.125 if "membrane" in code.name else 0.05
+    prm = L.params(precision=prec, quant_scale=qs or 2 ** -6, q=q, tick_budget=200, variant=variant)
+    _batch_vs_oracle(L, ctx, code, prm, 0.06, 160)
+
+
+def test_relaxed_multi_sweep_and_gauge(L, ctx):
+    """K = 2 sweeps per tick with alpha = dt/(K tau) = 0.5, and the gauge-on-move flag."""
+    code = I.toric2d(6)
+    prm = L.params(precision="f32", dt_tick=0.1, tau=0.1, sweeps_per_tick=2, tick_budget=120)
+    _batch_vs_oracle(L, ctx, code, prm, 0.06, 120)
+    prm = L.params(precision="f32", tick_budget=120, gauge_on_move=1)
+    _batch_vs_oracle(L, ctx, code, prm, 0.06, 120)
+    prm = L.params(precision="i16", tick_budget=120, gauge_on_move=1, dt_tick=0.05, variant="warp")
+    _batch_vs_oracle(L, ctx, I.toric3d_membrane(3), prm, 0.05, 80)
+
+
+def test_discrete_machine_on_a_quantum_code(L, ctx):
+    prm = L.params(feedback="bit_discrete", precision="f32", tick_budget=60, tau=0, dt_tick=0)
+    _batch_vs_oracle(L, ctx, I.toric2d(6), prm, 0.04, 100)
+
+
+def test_mixed_batch_and_launch_shape_invariance(L, ctx):
+    """Mixed codes, sizes and p in one launch; results equal per-point runs and do
+    not depend on block shape (randomness is keyed by (seed, point, shot))."""
+    codes = [I.bb_code(6, 6), I.bb_code(15, 3), I.bb_code(12, 6)]
+    lcs = [ctx.from_inputs(c) for c in codes]
+    prm = L.params(precision="i8", quant_scale=0.25, tick_budget=300)
+    pts = []
+    pid = 0
+    for lc in lcs:
+        for p in (0.02, 0.05, 0.08):
+            pts.append((lc, p, 40, 7, pid))
+            pid += 1
+    tal, rec = L.run_batch(ctx, pts, prm, 3)
+    off = 0
+    for (lc, p, n, s0, pid_), code in zip(pts, [c for c in codes for _ in range(3)]):
+        ora = oracle_point(code, prm, p, 3, pid_, s0, n)
+        compare_records(rec[off:off + n], ora, f"{code.name} p={p}")
+        off += n
+    for variant, bt in (("cta", 128), ("warp", 64), ("warp", 512)):
+        prm2 = L.params(precision="i8", quant_scale=0.25, tick_budget=300, variant=variant,
+                        block_threads=bt)
+        _, rec2 = L.run_batch(ctx, pts, prm2, 3)
+        assert np.array_equal(rec2, rec), (variant, bt)
+
+
+def test_trace_matches_oracle_every_tick(L, ctx):
+    code = I.toric2d(6)
+    lc = ctx.from_inputs(code)
+    prm = L.params(precision="f32", tick_budget=80)
+    oc = O.OracleCode.from_code(code)
+    op = oracle_params(prm)
+    for shot in range(6):
+        eh, sh, rec = L.trace(ctx, lc, prm, 0.07, 4, 1, shot, 80)
+        r = O.run_shot(oc, op, 0.07, 4, 1, shot, trace_ticks=80)
+        assert np.array_equal(_unpack(eh, code.n), r["trace"]["e_hist"]), shot
+        assert np.array_equal(_unpack(sh, code.m), r["trace"]["s_hist"]), shot
+        assert rec["t_clr"] == r["t_clr"]
+
+
+def test_edge_cases(L, ctx):
+    code = I.toric2d(8)
+    lc = ctx.from_inputs(code)
+    prm = L.params(precision="f32", tick_budget=32)
+    tal, rec = L.run_batch(ctx, [(lc, 0.0, 20, 0, 0), (lc, 1.0, 5, 0, 1), (lc, 0.05, 0, 0, 2)], prm, 1)
+    assert np.all(rec["t_clr"] == 0) and np.all(rec["moves"] == 0)
+    assert np.all(rec["failed"][:20] == 0)
+    assert np.all(rec["failed"][20:] == 0)  # all-ones on even L: winds an even number of times
+    assert tal[2]["shots"] == 0
+    # zero budget: every shot with a nonzero syndrome is a non-convergent failure
+    prm0 = L.params(precision="f32", tick_budget=0)
+    tal, rec = L.run_batch(ctx, [(lc, 0.1, 50, 0, 0)], prm0, 1)
+    ora = oracle_point(code, prm0, 0.1, 1, 0, 0, 50)
+    compare_records(rec, ora, "T=0")
+    # odd L: all-ones residual is a logical failure
+    code5 = I.toric2d(5)
+    tal, rec = L.run_batch(ctx, [(ctx.from_inputs(code5), 1.0, 3, 0, 0)], prm, 1)
+    assert np.all(rec["failed"] == 1) and np.all(rec["t_clr"] == 0)
+
+
+def test_ler_f32_agrees_with_fp64_oracle(L, ctx):
+    code = I.toric2d(8)
+    prm = L.params(precision="f32", tick_budget=32)
+    _, rec = L.run_batch(ctx, [(ctx.from_inputs(code), 0.05, 1000, 0, 0)], prm, 0)
+    ora = oracle_point(code, prm, 0.05, 0, 0, 0, 1000, precision="f64")
+    ok, bc = paired_ok(rec["failed"], ora["failed"])
+    assert ok, bc
+
+
+def test_sumproduct_ler_agrees_with_fp64_oracle(L, ctx):
+    code = I.toric2d(8)
+    prm = L.params(precision="f32", rule="sumproduct", tick_budget=64)
+    _, rec = L.run_batch(ctx, [(ctx.from_inputs(code), 0.06, 600, 0, 0)], prm, 2)
+    ora = oracle_point(code, prm, 0.06, 2, 0, 0, 600, precision="f64")
+    ok, bc = paired_ok(rec["failed"], ora["failed"])
+    assert ok, bc
+
+
+@pytest.mark.parametrize("L_,p,shots", [(128, 0.02, 3), (128, 0.12, 1), (64, 0.08, 3)])
+def test_full_size_toric2d_sampled(L, ctx, L_, p, shots):
+    """Full-size 2D toric shots (global-memory arena) in the benchmark's launch
+    configuration, against the oracle shot by shot."""
+    code = I.toric2d(L_)
+    prm = L.params(precision="f32", tick_budget=40 * L_, variant="cta")
+    _batch_vs_oracle(L, ctx, code, prm, p, shots, seed=0, point_id=5, shot0=1000, finals=False)
