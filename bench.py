@@ -40,10 +40,15 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
 
 
-def workload(name: str, shots: int):
+def workload(name: str, shots: int, sizes=None, ps=None):
+    """Points of a named workload; ``sizes``/``ps`` restrict it (profiling runs)."""
     w = I.WORKLOADS[name]
     pts = []
     for fam, size, p, pid in I.workload_points(name):
+        if sizes and str(size) not in sizes:
+            continue
+        if ps and not any(abs(p - float(x)) < 1e-9 for x in ps):
+            continue
         pts.append(dict(family=fam, size=size, p=p, point_id=pid, shots=shots,
                         T=I.tick_budget(w["budget"], size)))
     # most expensive points first: the queue hands out work in this order
@@ -187,13 +192,15 @@ def main():
     ap.add_argument("--workload", default="toric2d_sweep")
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--variant", default="auto")
-    ap.add_argument("--shots", type=int, default=16, help="shots per point per step")
+    ap.add_argument("--shots", type=int, default=32, help="shots per point per step")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--sizes", default="", help="comma list restricting the code sizes")
+    ap.add_argument("--ps", default="", help="comma list restricting the error rates")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -210,7 +217,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     ctx = L.Context(local)
-    w, pts = workload(args.workload, args.shots)
+    sizes = [x for x in args.sizes.split(",") if x]
+    ps = [x for x in args.ps.split(",") if x]
+    w, pts = workload(args.workload, args.shots, sizes, ps)
     codes = {}
     for d in pts:
         key = (d["family"], d["size"])

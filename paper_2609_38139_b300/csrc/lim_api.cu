@@ -114,7 +114,7 @@ struct Plan {
   size_t n_teams = 0;
   std::vector<const lim_code *> codes;
   std::vector<int> code_of_point;
-  std::vector<uint32_t> arena_smem;  // per code
+  std::vector<uint16_t> msg_smem, chk_smem;  // per code
   size_t workspace = 0;
 };
 
@@ -145,14 +145,17 @@ int make_plan(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_param
   int max_E = 0;
   for (auto *c : pl.codes) {
     lay.push_back(code_layout(c->dev, dp.prec));
-    max_bits = std::max(max_bits, lay.back().bits_bytes);
-    max_all = std::max(max_all, lay.back().bits_bytes + lay.back().arena_bytes);
+    const CodeLayout &l = lay.back();
+    max_bits = std::max(max_bits, l.bits_bytes);
+    max_all = std::max(max_all, l.bits_bytes + l.msg_bytes + l.chk_bytes);
     max_E = std::max(max_E, c->dev.E);
   }
   int variant = prm->variant;
   if (variant == LIM_VARIANT_PLAIN) return bad(LIM_E_UNSUPPORTED, "plain variant not built");
-  if (variant == LIM_VARIANT_AUTO) variant = (max_all <= 24 * 1024 && max_E <= 2048) ? LIM_VARIANT_WARP : LIM_VARIANT_CTA;
-  pl.arena_smem.assign(pl.codes.size(), 0);
+  if (variant == LIM_VARIANT_AUTO)
+    variant = (max_all <= 24 * 1024 && max_E <= 2048) ? LIM_VARIANT_WARP : LIM_VARIANT_CTA;
+  pl.msg_smem.assign(pl.codes.size(), 0);
+  pl.chk_smem.assign(pl.codes.size(), 0);
   if (variant == LIM_VARIANT_WARP) {
     pl.warp = 1;
     pl.block = prm->block_threads > 0 ? prm->block_threads : 256;
@@ -162,25 +165,37 @@ int make_plan(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_param
     pl.smem = pl.team_smem * teams;
     if (pl.smem > (size_t)ctx->smem_optin)
       return bad(LIM_E_UNSUPPORTED, "codes too large for one warp per shot; use LIM_VARIANT_CTA");
-    std::fill(pl.arena_smem.begin(), pl.arena_smem.end(), 1u);
+    std::fill(pl.msg_smem.begin(), pl.msg_smem.end(), 1);
+    std::fill(pl.chk_smem.begin(), pl.chk_smem.end(), 1);
     pl.slot_bytes = 0;
   } else {
     pl.warp = 0;
-    pl.block = prm->block_threads > 0 ? prm->block_threads : 512;
+    pl.block = prm->block_threads > 0 ? prm->block_threads : 1024;
     if (pl.block % 32 || pl.block > 1024) return bad(LIM_E_INVAL, "block_threads must be a multiple of 32, <= 1024");
-    const int target = prm->blocks_per_sm > 0 ? prm->blocks_per_sm : 2;
+    const int target = prm->blocks_per_sm > 0 ? prm->blocks_per_sm : 1;
     size_t cap = (size_t)ctx->smem_per_sm / target;
     cap = cap > 2048 ? cap - 2048 : cap;
     cap = std::min(cap, (size_t)ctx->smem_optin);
     if (max_bits > cap) return bad(LIM_E_UNSUPPORTED, "bit vectors of a code exceed shared memory");
     size_t team = max_bits, slot = 0;
     for (size_t i = 0; i < pl.codes.size(); i++) {
-      if (lay[i].bits_bytes + lay[i].arena_bytes <= cap) {
-        pl.arena_smem[i] = 1;
-        team = std::max(team, lay[i].bits_bytes + lay[i].arena_bytes);
+      const CodeLayout &l = lay[i];
+      size_t used = l.bits_bytes;
+      if (used + l.msg_bytes + l.chk_bytes <= cap) {
+        pl.msg_smem[i] = pl.chk_smem[i] = 1;
+        used += l.msg_bytes + l.chk_bytes;
+      } else if (used + l.msg_bytes <= cap) {
+        pl.msg_smem[i] = 1;
+        used += l.msg_bytes;
+        slot = std::max(slot, l.msg_bytes + l.chk_bytes);
+      } else if (used + l.chk_bytes <= cap) {
+        pl.chk_smem[i] = 1;
+        used += l.chk_bytes;
+        slot = std::max(slot, l.msg_bytes + l.chk_bytes);
       } else {
-        slot = std::max(slot, lay[i].arena_bytes);
+        slot = std::max(slot, l.msg_bytes + l.chk_bytes);
       }
+      team = std::max(team, used);
     }
     pl.team_smem = (team + 15) & ~size_t(15);
     pl.smem = pl.team_smem;
@@ -214,7 +229,8 @@ void fill_args(const Plan &pl, const lim_point *pts, uint32_t npts, const lim_pa
     d.shots = pts[i].shots;
     d.shot0 = pts[i].shot0;
     d.point_id = pts[i].point_id;
-    d.arena_smem = pl.arena_smem[d.code];
+    d.msg_smem = pl.msg_smem[d.code];
+    d.chk_smem = pl.chk_smem[d.code];
     d.p_thr = prob_threshold(pts[i].p);
     d.item0 = item;
     item += pts[i].shots;
@@ -233,7 +249,8 @@ int upload_code(lim_ctx *ctx, HostCode &hc, lim_code **out) {
   c->host = std::move(hc);
   const HostCode &h = c->host;
   const size_t nw = (h.n + 31) / 32;
-  const size_t words = (h.m + 1) + 3 * (size_t)h.E + (h.n + 1) + (size_t)h.k * nw;
+  // every table starts on a 16-byte boundary (rows are read with vector loads)
+  const size_t words = (h.m + 1) + 3 * (size_t)h.E + (h.n + 1) + (size_t)h.k * nw + 6 * 4;
   DevCode &d = c->dev;
   d.n = h.n;
   d.m = h.m;
@@ -243,6 +260,19 @@ int upload_code(lim_ctx *ctx, HostCode &hc, lim_code **out) {
   d.mw = (h.m + 31) / 32;
   d.dc_max = h.dc_max;
   d.dv_max = h.dv_max;
+  // degree classes (see lim_device.cuh): exact when every node has that degree
+  if (h.dv_min == h.dv_max && h.dv_max == 2) d.var_cls = 0;
+  else if (h.dv_min == h.dv_max && h.dv_max == 3) d.var_cls = 1;
+  else if (h.dv_min == h.dv_max && h.dv_max == 4) d.var_cls = 2;
+  else if (h.dv_max <= 2) d.var_cls = 3;
+  else if (h.dv_max <= 4) d.var_cls = 4;
+  else d.var_cls = 5;
+  if (h.dc_min == h.dc_max && h.dc_max == 2) d.chk_cls = 0;
+  else if (h.dc_min == h.dc_max && h.dc_max == 4) d.chk_cls = 1;
+  else if (h.dc_min == h.dc_max && h.dc_max == 6) d.chk_cls = 2;
+  else if (h.dc_max <= 4) d.chk_cls = 3;
+  else if (h.dc_max <= 6) d.chk_cls = 4;
+  else d.chk_cls = 5;
   if (ctx->device < 0) {  // host-only context
     *out = c;
     return LIM_OK;
@@ -258,6 +288,7 @@ int upload_code(lim_ctx *ctx, HostCode &hc, lim_code **out) {
   auto put = [&buf](const std::vector<int32_t> &v) {
     size_t o = buf.size();
     buf.insert(buf.end(), v.begin(), v.end());
+    while (buf.size() % 4) buf.push_back(0);
     return o;
   };
   size_t o_cptr = put(h.c_ptr), o_cvar = put(h.c_var), o_vptr = put(h.v_ptr), o_vedge = put(h.v_edge),

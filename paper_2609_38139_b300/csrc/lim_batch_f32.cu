@@ -1,0 +1,11 @@
+// lim_batch_f32.cu -- batch kernels with f32 message storage.
+#include "lim_batch.cuh"
+
+namespace lim {
+
+const void *batch_fn_f32(int warp, int rule, int fb) {
+  using namespace batch_detail;
+  return warp ? pick_kernel<TeamWarp, LIM_PREC_F32>(rule, fb) : pick_kernel<TeamCTA, LIM_PREC_F32>(rule, fb);
+}
+
+}  // namespace lim

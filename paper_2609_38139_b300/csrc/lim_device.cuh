@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "lim_internal.h"
 
@@ -156,67 +157,192 @@ __device__ __forceinline__ float boxplus(float a, float b) {
 // s~_c = s_c + sum_{w in N(c)} sigma_w (gauge covariance, Sec. S2).
 // ---------------------------------------------------------------------------
 
+// Degree classes: the paper's codes are regular (every qubit in DV checks,
+// every check on DC qubits), so the half-sweeps are compiled per degree with
+// all per-edge values in registers.  Irregular codes (the open chain's end
+// qubits) use an upper bound with a runtime degree.
+enum : int32_t {
+  kVar2 = 0, kVar3 = 1, kVar4 = 2, kVarLe2 = 3, kVarLe4 = 4, kVarLe8 = 5,
+};
+enum : int32_t {
+  kChk2 = 0, kChk4 = 1, kChk6 = 2, kChkLe4 = 3, kChkLe6 = 4, kChkLe8 = 5,
+};
+
+// Loads / stores N consecutive messages with the widest aligned vector accesses
+// (a row of a regular code starts at a multiple of N elements).
+template <int BYTES>
+struct VecOf;
+template <> struct VecOf<16> { using V = int4; };
+template <> struct VecOf<8> { using V = int2; };
+template <> struct VecOf<4> { using V = int; };
+template <> struct VecOf<2> { using V = short; };
+template <> struct VecOf<1> { using V = char; };
+
+template <class T, int N>
+struct RowIO {
+  static constexpr int BYTES = N * (int)sizeof(T);
+  static constexpr int VB = (BYTES % 16 == 0) ? 16 : (BYTES % 8 == 0) ? 8 : (BYTES % 4 == 0) ? 4
+                          : (BYTES % 2 == 0) ? 2 : 1;
+  using V = typename VecOf<VB>::V;
+  static constexpr int NV = BYTES / VB;
+  __device__ static __forceinline__ void load(const T *p, T (&out)[N]) {
+    V tmp[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) tmp[k] = reinterpret_cast<const V *>(p)[k];
+    memcpy(out, tmp, BYTES);
+  }
+  __device__ static __forceinline__ void store(T *p, const T (&in)[N]) {
+    V tmp[NV];
+    memcpy(tmp, in, BYTES);
+#pragma unroll
+    for (int k = 0; k < NV; k++) reinterpret_cast<V *>(p)[k] = tmp[k];
+  }
+};
+
+// Everything the bit-centric read-out needs to apply its flips in place.
+struct FlipCtx {
+  uint32_t *e, *s, *sg;
+  int32_t *defects, *moves;
+};
+
+__device__ __forceinline__ void flip_bits(const DevCode &C, const FlipCtx &F, int v) {
+  atomicXor(F.e + (v >> 5), 1u << (v & 31));
+  const int b = __ldg(C.v_ptr + v), en = __ldg(C.v_ptr + v + 1);
+  int delta = 0;
+  for (int t = b; t < en; t++) {
+    const int c = __ldg(C.v_chk + t);
+    const uint32_t bit = 1u << (c & 31);
+    const uint32_t old = atomicXor(F.s + (c >> 5), bit);
+    delta += (old & bit) ? -1 : 1;
+  }
+  atomicAdd(F.defects, delta);
+  atomicAdd(F.moves, 1);
+}
+
 // Eq. 1 for every edge of qubit v: VCn[e] = update(VCc[e], pi + sum_{c' != c} CV[c'->v]),
-// summed in ascending check order.  Returns the read-out sum pi + sum_c CV (Eq. 3).
-template <int PREC>
-__device__ __forceinline__ typename MT<PREC>::A var_update(const DevCode &C, const DevParams &P,
-                                                           int v, const typename MT<PREC>::T *CV,
-                                                           const typename MT<PREC>::T *VCc,
-                                                           typename MT<PREC>::T *VCn) {
+// summed in ascending check order (the order of N(v)).  With READOUT also
+// Eq. 3, L_v = pi + sum_c CV[c->v], and the bit-centric feedback f_v = 1[L_v > 0]
+// applied in the actual frame (-1)^{sigma_v} (Sec. S2).
+template <int PREC, int DV, bool EXACT, bool READOUT>
+__device__ __forceinline__ void var_one(const DevCode &C, const DevParams &P, int v,
+                                        const typename MT<PREC>::T *__restrict__ CV,
+                                        const typename MT<PREC>::T *__restrict__ VCc,
+                                        typename MT<PREC>::T *__restrict__ VCn, const FlipCtx &F) {
   using M = MT<PREC>;
   using A = typename M::A;
-  const int b = __ldg(C.v_ptr + v);
-  const int d = __ldg(C.v_ptr + v + 1) - b;
-  A cv[kMaxDeg];
-  int ed[kMaxDeg];
-#pragma unroll
-  for (int j = 0; j < kMaxDeg; j++) {
-    if (j < d) {
-      ed[j] = __ldg(C.v_edge + b + j);
-      cv[j] = M::ld(CV + ed[j]);
-    }
+  int b, d;
+  if (EXACT) {
+    b = v * DV;
+    d = DV;
+  } else {
+    b = __ldg(C.v_ptr + v);
+    d = __ldg(C.v_ptr + v + 1) - b;
   }
+  int ed[DV];
+  if (EXACT && (DV == 2 || DV == 4)) {
+    int tmp[DV];
+    RowIO<int, DV>::load(C.v_edge + b, tmp);
+#pragma unroll
+    for (int j = 0; j < DV; j++) ed[j] = tmp[j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < DV; j++) ed[j] = (EXACT || j < d) ? __ldg(C.v_edge + b + j) : 0;
+  }
+  A cv[DV];
+#pragma unroll
+  for (int j = 0; j < DV; j++) cv[j] = (EXACT || j < d) ? M::ld(CV + ed[j]) : A(0);
   const A pi = prior<A>(P);
 #pragma unroll
-  for (int j = 0; j < kMaxDeg; j++) {
-    if (j < d) {
+  for (int j = 0; j < DV; j++) {
+    if (EXACT || j < d) {
       A acc = pi;
 #pragma unroll
-      for (int jj = 0; jj < kMaxDeg; jj++)
-        if (jj < d && jj != j) acc = wadd(acc, cv[jj]);
+      for (int jj = 0; jj < DV; jj++)
+        if (jj != j && (EXACT || jj < d)) acc = wadd(acc, cv[jj]);
       const A old = P.alpha_is_one ? A(0) : M::ld(VCc + ed[j]);
       M::st(VCn + ed[j], update(P, old, acc));
     }
   }
-  A L = pi;
+  if (READOUT) {
+    A L = pi;
 #pragma unroll
-  for (int jj = 0; jj < kMaxDeg; jj++)
-    if (jj < d) L = wadd(L, cv[jj]);
-  return L;
+    for (int jj = 0; jj < DV; jj++)
+      if (EXACT || jj < d) L = wadd(L, cv[jj]);
+    const uint32_t bit = 1u << (v & 31);
+    const bool sgn = (F.sg[v >> 5] & bit) != 0;
+    if ((sgn ? -L : L) > A(0)) {
+      flip_bits(C, F, v);
+      atomicXor(F.sg + (v >> 5), bit);
+    }
+  }
 }
 
-// Eq. 2 for every edge of check c, in place on CV (CV is not read by anything
-// else during the check half-sweep).  sbit = s~_c.
-template <int PREC, int RULE>
-__device__ __forceinline__ void check_update(const DevCode &C, const DevParams &P, int c, int sbit,
-                                             const typename MT<PREC>::T *VCc,
-                                             typename MT<PREC>::T *CV) {
+template <int PREC, int DV, bool EXACT, bool READOUT>
+__device__ __forceinline__ void var_loop(int rank, int size, const DevCode &C, const DevParams &P,
+                                         const typename MT<PREC>::T *CV,
+                                         const typename MT<PREC>::T *VCc, typename MT<PREC>::T *VCn,
+                                         const FlipCtx &F) {
+  int v = rank;
+  for (; v + size < C.n; v += 2 * size) {  // two qubits per iteration: independent loads overlap
+    var_one<PREC, DV, EXACT, READOUT>(C, P, v, CV, VCc, VCn, F);
+    var_one<PREC, DV, EXACT, READOUT>(C, P, v + size, CV, VCc, VCn, F);
+  }
+  if (v < C.n) var_one<PREC, DV, EXACT, READOUT>(C, P, v, CV, VCc, VCn, F);
+}
+
+// The qubit half-sweep over all qubits of the code.
+template <int PREC, bool READOUT>
+__device__ __noinline__ void var_pass(int rank, int size, const DevCode &C, const DevParams &P,
+                                      const typename MT<PREC>::T *CV,
+                                      const typename MT<PREC>::T *VCc, typename MT<PREC>::T *VCn,
+                                      FlipCtx F) {
+  switch (C.var_cls) {
+    case kVar2: var_loop<PREC, 2, true, READOUT>(rank, size, C, P, CV, VCc, VCn, F); break;
+    case kVar3: var_loop<PREC, 3, true, READOUT>(rank, size, C, P, CV, VCc, VCn, F); break;
+    case kVar4: var_loop<PREC, 4, true, READOUT>(rank, size, C, P, CV, VCc, VCn, F); break;
+    case kVarLe2: var_loop<PREC, 2, false, READOUT>(rank, size, C, P, CV, VCc, VCn, F); break;
+    case kVarLe4: var_loop<PREC, 4, false, READOUT>(rank, size, C, P, CV, VCc, VCn, F); break;
+    default: var_loop<PREC, 8, false, READOUT>(rank, size, C, P, CV, VCc, VCn, F); break;
+  }
+}
+
+// Eq. 2 for every edge of check c, in place on CV (nothing else reads CV during
+// the check half-sweep).  sbit = s~_c.  Min-sum: sign product times the minimum
+// magnitude over the other edges (min1/min2); sum-product: prefix/suffix
+// box-plus products exclude each edge without division.
+template <int PREC, int RULE, int DC, bool EXACT>
+__device__ __forceinline__ void check_one(const DevCode &C, const DevParams &P, int c, int sbit,
+                                          const typename MT<PREC>::T *__restrict__ VCc,
+                                          typename MT<PREC>::T *__restrict__ CV) {
   using M = MT<PREC>;
+  using T = typename M::T;
   using A = typename M::A;
-  const int b = __ldg(C.c_ptr + c);
-  const int d = __ldg(C.c_ptr + c + 1) - b;
-  A x[kMaxDeg];
+  int b, d;
+  if (EXACT) {
+    b = c * DC;
+    d = DC;
+  } else {
+    b = __ldg(C.c_ptr + c);
+    d = __ldg(C.c_ptr + c + 1) - b;
+  }
+  A x[DC];
+  if (EXACT) {
+    T raw[DC];
+    RowIO<T, DC>::load(VCc + b, raw);
 #pragma unroll
-  for (int j = 0; j < kMaxDeg; j++)
-    if (j < d) x[j] = M::ld(VCc + b + j);
-  int neg = (sbit + d) & 1;  // (-1)^{s_c + d_c}
-  A out[kMaxDeg];
+    for (int j = 0; j < DC; j++) x[j] = M::ld(raw + j);
+  } else {
+#pragma unroll
+    for (int j = 0; j < DC; j++) x[j] = (j < d) ? M::ld(VCc + b + j) : A(0);
+  }
+  A out[DC];
   if (RULE == LIM_RULE_MINSUM || M::is_int) {
+    int neg = (sbit + d) & 1;  // (-1)^{s_c + d_c}
     A min1 = inf_of(A(0)), min2 = inf_of(A(0));
     int imin = -1;
 #pragma unroll
-    for (int j = 0; j < kMaxDeg; j++) {
-      if (j < d) {
+    for (int j = 0; j < DC; j++) {
+      if (EXACT || j < d) {
         const A a = absw(x[j]);
         neg ^= (x[j] < A(0));
         if (a < min1) {
@@ -229,46 +355,93 @@ __device__ __forceinline__ void check_update(const DevCode &C, const DevParams &
       }
     }
 #pragma unroll
-    for (int j = 0; j < kMaxDeg; j++) {
-      if (j < d) {
-        const A mag = (j == imin) ? min2 : min1;
-        const bool ng = neg ^ (x[j] < A(0));
-        out[j] = (mag == A(0)) ? A(0) : (ng ? -mag : mag);
-      }
+    for (int j = 0; j < DC; j++) {
+      const A mag = (j == imin) ? min2 : min1;
+      const bool ng = neg ^ (x[j] < A(0));
+      out[j] = (mag == A(0)) ? A(0) : (ng ? -mag : mag);
     }
   } else {
     if constexpr (!M::is_int) {
-      // prefix/suffix box-plus products exclude each edge without division
-      float pre[kMaxDeg], suf[kMaxDeg];
+      float pre[DC], suf[DC];
 #pragma unroll
-      for (int j = 0; j < kMaxDeg; j++)
-        if (j < d) pre[j] = (j == 0) ? x[0] : boxplus(pre[j - 1], x[j]);
+      for (int j = 0; j < DC; j++) pre[j] = (j == 0) ? x[0] : boxplus(pre[j - 1], x[j]);
+      // suffix products ending at the row's last valid edge
 #pragma unroll
-      for (int j = kMaxDeg - 1; j >= 0; j--)
-        if (j < d) suf[j] = (j == d - 1) ? x[d - 1] : boxplus(x[j], suf[j + 1]);
+      for (int j = DC - 1; j >= 0; j--) {
+        if (EXACT) suf[j] = (j == DC - 1) ? x[j] : boxplus(x[j], suf[j + 1]);
+        else suf[j] = (j >= d - 1) ? x[j] : boxplus(x[j], suf[j + 1]);
+      }
       const float sg = (((sbit + d) & 1) ? -1.f : 1.f);
 #pragma unroll
-      for (int j = 0; j < kMaxDeg; j++) {
-        if (j < d) {
-          float g;
-          if (d == 1) g = inf_of(0.f);
-          else if (j == 0) g = suf[1];
-          else if (j == d - 1) g = pre[d - 2];
-          else g = boxplus(pre[j - 1], suf[j + 1]);
-          g = sg * g;
-          out[j] = (g == 0.f) ? 0.f : g;
-        }
+      for (int j = 0; j < DC; j++) {
+        float g;
+        if (d == 1) g = inf_of(0.f);
+        else if (j == 0) g = suf[1];
+        else if (j == d - 1) g = pre[j - 1];
+        else g = boxplus(pre[j - 1], suf[(j + 1 < DC) ? j + 1 : j]);
+        g = sg * g;
+        out[j] = (g == 0.f) ? 0.f : g;
       }
     }
   }
+  if (EXACT) {
+    T res[DC];
+    if (P.alpha_is_one) {
 #pragma unroll
-  for (int j = 0; j < kMaxDeg; j++) {
-    if (j < d) {
-      const A old = P.alpha_is_one ? A(0) : M::ld(CV + b + j);
-      M::st(CV + b + j, update(P, old, out[j]));
+      for (int j = 0; j < DC; j++) M::st(res + j, update(P, A(0), out[j]));
+    } else {
+      T old[DC];
+      RowIO<T, DC>::load(CV + b, old);
+#pragma unroll
+      for (int j = 0; j < DC; j++) M::st(res + j, update(P, M::ld(old + j), out[j]));
+    }
+    RowIO<T, DC>::store(CV + b, res);
+  } else {
+#pragma unroll
+    for (int j = 0; j < DC; j++) {
+      if (j < d) {
+        const A old = P.alpha_is_one ? A(0) : M::ld(CV + b + j);
+        M::st(CV + b + j, update(P, old, out[j]));
+      }
     }
   }
 }
+
+template <int PREC, int RULE, int DC, bool EXACT, class SBit>
+__device__ __forceinline__ void check_loop(int rank, int size, const DevCode &C, const DevParams &P,
+                                           const SBit &sbit, const typename MT<PREC>::T *VCc,
+                                           typename MT<PREC>::T *CV) {
+  int c = rank;
+  for (; c + size < C.m; c += 2 * size) {
+    check_one<PREC, RULE, DC, EXACT>(C, P, c, sbit(c), VCc, CV);
+    check_one<PREC, RULE, DC, EXACT>(C, P, c + size, sbit(c + size), VCc, CV);
+  }
+  if (c < C.m) check_one<PREC, RULE, DC, EXACT>(C, P, c, sbit(c), VCc, CV);
+}
+
+// The check half-sweep over all checks; sbit(c) returns s~_c.
+template <int PREC, int RULE, class SBit>
+__device__ __noinline__ void check_pass(int rank, int size, const DevCode &C, const DevParams &P,
+                                        SBit sbit, const typename MT<PREC>::T *VCc,
+                                        typename MT<PREC>::T *CV) {
+  switch (C.chk_cls) {
+    case kChk2: check_loop<PREC, RULE, 2, true>(rank, size, C, P, sbit, VCc, CV); break;
+    case kChk4: check_loop<PREC, RULE, 4, true>(rank, size, C, P, sbit, VCc, CV); break;
+    case kChk6: check_loop<PREC, RULE, 6, true>(rank, size, C, P, sbit, VCc, CV); break;
+    case kChkLe4: check_loop<PREC, RULE, 4, false>(rank, size, C, P, sbit, VCc, CV); break;
+    case kChkLe6: check_loop<PREC, RULE, 6, false>(rank, size, C, P, sbit, VCc, CV); break;
+    default: check_loop<PREC, RULE, 8, false>(rank, size, C, P, sbit, VCc, CV); break;
+  }
+}
+
+struct SBitWords {  // s~ from bit-packed words
+  const uint32_t *w;
+  __device__ __forceinline__ int operator()(int c) const { return (w[c >> 5] >> (c & 31)) & 1; }
+};
+struct SBitBytes {  // s from one byte per check
+  const uint8_t *b;
+  __device__ __forceinline__ int operator()(int c) const { return b[c] & 1; }
+};
 
 // Read-out of Eq. 3 for qubit v in the stored frame: pi + sum_c CV[c->v].
 template <int PREC>

@@ -28,6 +28,7 @@ struct DevCode {
   int32_t n, m, E, k;
   int32_t nw, mw;              // words of the bit vectors e and s
   int32_t dc_max, dv_max;
+  int32_t var_cls, chk_cls;    // degree classes of the half-sweeps
   const int32_t *c_ptr;        // [m+1]
   const int32_t *c_var;        // [E]
   const int32_t *v_ptr;        // [n+1]
@@ -42,7 +43,8 @@ struct DevPoint {
   uint32_t shots;
   uint32_t shot0;
   uint32_t point_id;
-  uint32_t arena_smem; // 1: message arena of this code lives in shared memory
+  uint16_t msg_smem;   // 1: this code's messages live in shared memory
+  uint16_t chk_smem;   // 1: its per-check feedback scratch lives in shared memory
   uint64_t p_thr;      // floor(p * 2^32), 2^32 for p >= 1
   uint64_t item0;      // first work item of this point
 };
@@ -81,8 +83,9 @@ struct LaunchArgs {
 
 // Per-code sizes used to lay out team memory.
 struct CodeLayout {
-  size_t bits_bytes;   // e, s, s0, sigma bit vectors (always shared memory)
-  size_t arena_bytes;  // messages + per-check feedback scratch
+  size_t bits_bytes;   // control block + e, s, s0, sigma bit vectors (always shared memory)
+  size_t msg_bytes;    // CV, VC (two buffers)
+  size_t chk_bytes;    // per-check feedback scratch
 };
 
 size_t msg_bytes(int prec);
