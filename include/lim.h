@@ -216,6 +216,23 @@ int lim_run_batch(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_p
                   uint64_t seed, void *workspace, size_t workspace_bytes, lim_shot_record *rec,
                   uint32_t *e_final, lim_tally *tally, void *stream);
 
+/* lim_run_batch without any device allocation, for callers that cannot call
+ * cudaMalloc while they run (a real-time loop that must not block on the
+ * allocator, memory owned by another framework's pool, launches being recorded
+ * into a CUDA graph).  The paper has no counterpart: this is an interface
+ * convenience.  The workspace is a 64 MiB array inside the library, held by
+ * every device that loads the library until the process exits; batches whose
+ * lim_workspace_size() exceeds 64 MiB are refused with LIM_E_NOMEM (use
+ * lim_run_batch).  The first call on a device looks up the array's device
+ * address with that device current, so make that first call before any stream
+ * capture.  Every call uses the same array: calls whose kernels overlap on the
+ * GPU (other streams, other threads) race and give wrong results; serialise
+ * them.  Each call clears the work-queue counter itself; nothing else of the
+ * array needs to start at zero.  Other arguments and results as lim_run_batch. */
+int lim_run_batch_static(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+                         uint64_t seed, lim_shot_record *rec, uint32_t *e_final, lim_tally *tally,
+                         void *stream);
+
 /* Words per shot of lim_run_batch's e_final rows for this point list. */
 int lim_final_words(const lim_point *pts, uint32_t npts, int32_t *words);
 

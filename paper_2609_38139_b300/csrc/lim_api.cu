@@ -7,6 +7,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -600,3 +601,82 @@ int lim_readout(const lim_code *code, const lim_params *prm, uint32_t nstates, c
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batch runs without any device allocation.
+//
+// Some callers cannot call cudaMalloc while they run trajectories: a real-time
+// controller that must not block (cudaMalloc may synchronise the device), a
+// process whose device memory is owned by another framework's pool, or code
+// that records its launches into a CUDA graph (cudaMalloc is not allowed during
+// stream capture).  lim_run_batch_static serves them with a workspace that lives
+// in this file-scope array instead of a caller-provided buffer.  The array is
+// allocated when the library is loaded and every device that loads it holds it
+// until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticWorkspaceBytes = size_t(64) << 20;  // 64 MiB
+__device__ __align__(256) uint8_t g_static_workspace[kStaticWorkspaceBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_workspace on `device`, looked up once per device
+// with that device current (the host-side symbol is only a stand-in).
+int static_workspace(int device, void **out) {
+  if (device < 0 || device >= kMaxDevices) return bad(LIM_E_INVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[device]) {
+    int prev = -1;
+    cudaError_t err = cudaGetDevice(&prev);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaGetDevice");
+    err = cudaSetDevice(device);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaSetDevice");
+    void *p = nullptr;
+    err = cudaGetSymbolAddress(&p, g_static_workspace);
+    cudaError_t err2 = cudaSetDevice(prev);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaGetSymbolAddress(static workspace)");
+    if (err2 != cudaSuccess) return cuda_fail(err2, "cudaSetDevice(restore)");
+    g_static_addr[device] = p;
+  }
+  *out = g_static_addr[device];
+  return LIM_OK;
+}
+
+}  // namespace
+
+extern "C" int lim_run_batch_static(lim_ctx *ctx, const lim_point *pts, uint32_t npts,
+                                    const lim_params *prm, uint64_t seed, lim_shot_record *rec,
+                                    uint32_t *e_final, lim_tally *tally, void *stream) {
+  return guarded([&] {
+    if (!ctx || !tally) return bad(LIM_E_INVAL, "null context or tally");
+    if (ctx->device < 0) return bad(LIM_E_INVAL, "host-only context cannot run kernels");
+    DevParams dp;
+    int st = derive(prm, dp);
+    if (st) return st;
+    Plan pl;
+    st = make_plan(ctx, pts, npts, prm, dp, pl);
+    if (st) return st;
+    if (pl.workspace > kStaticWorkspaceBytes)
+      return bad(LIM_E_NOMEM, "this batch needs more workspace than the 64 MiB static array; "
+                              "use lim_run_batch with a caller buffer");
+    void *ws = nullptr;
+    st = static_workspace(ctx->device, &ws);
+    if (st) return st;
+    LaunchArgs a;
+    fill_args(pl, pts, npts, prm, dp, seed, ws, a);
+    a.rec = rec;
+    a.e_final = e_final;
+    if (e_final) lim_final_words(pts, npts, &a.e_final_words);
+    a.tally = tally;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the queue counter must start at zero; the rest of the array is scratch
+    cudaError_t err = cudaMemsetAsync(ws, 0, 256, s);
+    if (err == cudaSuccess) err = cudaMemsetAsync(tally, 0, sizeof(lim_tally) * npts, s);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync");
+    if (a.total_items == 0) return LIM_OK;
+    return launch_batch(a, pl.warp, pl.grid, pl.block, pl.smem, stream);
+  });
+}

@@ -32,8 +32,8 @@ MAX_POINTS = 128
 EXPORTS = ["lim_last_error", "lim_version", "lim_ctx_create", "lim_ctx_destroy", "lim_code_from_csr",
            "lim_code_rep", "lim_code_toric2d", "lim_code_toric3d", "lim_code_bb", "lim_code_info",
            "lim_code_export", "lim_code_destroy", "lim_sample_noise", "lim_params_check",
-           "lim_workspace_size", "lim_run_batch", "lim_final_words", "lim_trace", "lim_bp_sweeps",
-           "lim_readout"]
+           "lim_workspace_size", "lim_run_batch", "lim_run_batch_static", "lim_final_words",
+           "lim_trace", "lim_bp_sweeps", "lim_readout"]
 
 
 class LimError(RuntimeError):
@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
     L.lim_workspace_size.argtypes = [vp, vp, u32, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]
     L.lim_run_batch.argtypes = [vp, vp, u32, ctypes.POINTER(Params), u64, vp, ctypes.c_size_t, vp, vp,
                                 vp, vp]
+    L.lim_run_batch_static.argtypes = [vp, vp, u32, ctypes.POINTER(Params), u64, vp, vp, vp, vp]
     L.lim_final_words.argtypes = [vp, u32, ctypes.POINTER(i32)]
     L.lim_trace.argtypes = [vp, vp, ctypes.POINTER(Params), dbl, u64, u32, u32, i32, vp,
                             ctypes.c_size_t, vp, vp, vp, vp]
@@ -304,6 +305,26 @@ def run_batch(ctx: Context, points, prm: Params, seed: int, e_final: bool = Fals
     torch.cuda.synchronize(ctx.device)
     out = (b.tallies(), b.records())
     return out + ((b.finals(),) if e_final else ())
+
+
+def run_batch_static(ctx: Context, points, prm: Params, seed: int, stream=None):
+    """``run_batch`` through ``lim_run_batch_static``: the library's own 64 MiB
+    device workspace instead of a buffer from the caller, for callers that cannot
+    allocate device memory while they run.  Output buffers still come from the
+    caller (here: torch).  Returns (tallies, records) on the host."""
+    import torch
+    pts = _points(points)
+    nshots = sum(int(p[2]) for p in points)
+    dev = torch.device("cuda", ctx.device)
+    tally = torch.zeros(len(points) * TALLY_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    rec = torch.empty(max(nshots, 1) * RECORD_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    check(lib().lim_run_batch_static(ctx.handle, pts, len(points), ctypes.byref(prm), int(seed),
+                                     rec.data_ptr(), None, tally.data_ptr(), _stream_ptr(stream)),
+          "lim_run_batch_static")
+    torch.cuda.synchronize(ctx.device)
+    t = np.frombuffer(tally.cpu().numpy().tobytes(), dtype=TALLY_DTYPE).copy()
+    r = np.frombuffer(rec.cpu().numpy().tobytes()[:nshots * RECORD_DTYPE.itemsize], dtype=RECORD_DTYPE).copy()
+    return t, r
 
 
 def sample_noise(code: Code, p: float, seed: int, point_id: int, shot0: int, nshots: int, stream=None):
