@@ -199,6 +199,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--phases", action="store_true", help="report the kernel's per-phase cycle shares")
     ap.add_argument("--sizes", default="", help="comma list restricting the code sizes")
     ap.add_argument("--ps", default="", help="comma list restricting the error rates")
     args = ap.parse_args()
@@ -228,6 +229,7 @@ def main():
     prm = lib_params(L, w, args.workload, args.precision, args.variant)
     prm.block_threads = args.block_threads
     prm.blocks_per_sm = args.blocks_per_sm
+    prm.profile = 1 if args.phases else 0
     # weak scaling: every rank runs its own disjoint shot ids of every point
     def step_points(step):
         base = (step * world + rank) * args.shots
@@ -270,8 +272,10 @@ def main():
     ms = [a.elapsed_time(b) for a, b in evs]
     tot_ms = sum(ms)
     ticks = upd = shots = fails = 0
+    phase = np.zeros(len(L.PHASES))
     for t in tallies:
         arr = np.frombuffer(t.cpu().numpy().tobytes(), dtype=L.TALLY_DTYPE)
+        phase += arr["phase_cycles"].sum(axis=0)
         ticks += int(arr["ticks"].sum())
         upd += int(arr["msg_updates"].sum())
         shots += int(arr["shots"].sum())
@@ -308,6 +312,9 @@ def main():
                          "kernel": "batch_kernel (persistent)",
                          "algorithmic_bytes": "2 x msg bytes per message update (read old, write new)"},
             "clocks": clk, "gpu_launches": args.steps}
+    if args.phases and phase.sum() > 0:
+        line["phase_share"] = {n: round(float(v / phase.sum()), 4) for n, v in zip(L.PHASES, phase)}
+        line["phase_cycles_per_tick"] = float(phase.sum() / max(1, ticks))
     # end to end through the public API: run + read records and tallies back
     if not args.no_e2e:
         rec_host = torch.empty(batch.rec.numel(), dtype=torch.uint8, pin_memory=True)

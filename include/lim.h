@@ -85,6 +85,9 @@ extern "C" {
 #define LIM_MAX_POINTS 128 /* points per lim_run_batch call                    */
 #define LIM_MAX_CODES 16   /* distinct codes per lim_run_batch call            */
 #define LIM_HIST_BINS 24   /* t_clr histogram: bin 0 = t_clr 0, bin b = [2^(b-1), 2^b) */
+#define LIM_PHASES 6       /* profiled phases: init, read-out/feedback scan + qubit
+                              half-sweep, move resolution, check half-sweep, further
+                              sweeps, finish                                        */
 
 typedef struct lim_ctx lim_ctx;
 typedef struct lim_code lim_code;
@@ -114,6 +117,7 @@ typedef struct {
   int32_t variant;         /* LIM_VARIANT_*                                         */
   int32_t block_threads;   /* 0 = library default                                   */
   int32_t blocks_per_sm;   /* 0 = as many as fit                                    */
+  int32_t profile;         /* 1: accumulate clock cycles per phase into the tally   */
 } lim_params;
 
 typedef struct {
@@ -143,6 +147,7 @@ typedef struct {
   int64_t msg_updates;        /* sweeps * 2E                                       */
   int64_t errors;             /* device-side internal errors (must be 0)          */
   int64_t hist[LIM_HIST_BINS];/* t_clr histogram of converged shots               */
+  int64_t phase_cycles[LIM_PHASES]; /* SM clock cycles per phase (lim_params.profile) */
 } lim_tally;
 
 /* Last error message of the calling thread ("" if none). */

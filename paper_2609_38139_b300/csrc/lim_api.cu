@@ -19,6 +19,7 @@ struct lim_ctx {
   int num_sms;
   int smem_optin;      // max dynamic shared memory per block
   int smem_per_sm;
+  int *pinned = nullptr;  // host word polled by the plain path
 };
 
 struct lim_code {
@@ -83,6 +84,7 @@ int derive(const lim_params *p, DevParams &o) {
   o.K = p->sweeps_per_tick;
   o.gauge_on_move = (p->feedback == LIM_FB_CHECK_MOVE) && p->gauge_on_move ? 1 : 0;
   o.alpha_is_one = alpha == 1.0;
+  o.profile = p->profile ? 1 : 0;
   const double pi = std::log(p->q / (1.0 - p->q));
   if (is_int) {
     if (!(p->quant_scale > 0.0)) return bad(LIM_E_INVAL, "quant_scale must be > 0");
@@ -106,6 +108,7 @@ int derive(const lim_params *p, DevParams &o) {
 }
 
 struct Plan {
+  int plain = 0;
   int warp = 0;
   int block = 0;
   int grid = 0;
@@ -152,7 +155,18 @@ int make_plan(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_param
     max_E = std::max(max_E, c->dev.E);
   }
   int variant = prm->variant;
-  if (variant == LIM_VARIANT_PLAIN) return bad(LIM_E_UNSUPPORTED, "plain variant not built");
+  if (variant == LIM_VARIANT_PLAIN) {
+    // one block per shot, every array in HBM, one point at a time
+    if (dp.prec != LIM_PREC_F32) return bad(LIM_E_UNSUPPORTED, "the plain path supports f32 only");
+    pl.plain = 1;
+    pl.block = prm->block_threads > 0 ? prm->block_threads : 256;
+    if (pl.block % 32 || pl.block > 1024) return bad(LIM_E_INVAL, "block_threads must be a multiple of 32, <= 1024");
+    size_t most = 0;
+    for (uint32_t i = 0; i < npts; i++)
+      most = std::max(most, (size_t)pts[i].shots * plain_slot_bytes(pts[i].code->dev, dp.prec));
+    pl.workspace = kWsHeader + most;
+    return LIM_OK;
+  }
   if (variant == LIM_VARIANT_AUTO)
     variant = (max_all <= 24 * 1024 && max_E <= 2048) ? LIM_VARIANT_WARP : LIM_VARIANT_CTA;
   pl.msg_smem.assign(pl.codes.size(), 0);
@@ -243,6 +257,66 @@ void fill_args(const Plan &pl, const lim_point *pts, uint32_t npts, const lim_pa
   a.queue = (unsigned long long *)ws;
 }
 
+// The plain baseline: for each point, one init launch, then one launch per tick
+// with the number of still-running shots read back after every tick (the host
+// decides termination), then one finish launch.  Synchronous on the host.
+int run_plain(lim_ctx *ctx, const Plan &pl, const lim_point *pts, uint32_t npts,
+              const lim_params *prm, const DevParams &dp, uint64_t seed, void *ws,
+              lim_shot_record *rec, uint32_t *e_final, lim_tally *tally, void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!ctx->pinned) {
+    cudaError_t err = cudaMallocHost((void **)&ctx->pinned, sizeof(int));
+    if (err != cudaSuccess) return cuda_fail(err, "cudaMallocHost");
+  }
+  int32_t words = 0;
+  if (e_final) lim_final_words(pts, npts, &words);
+  int *running = (int *)((uint8_t *)ws + 256);
+  uint64_t item0 = 0;
+  for (uint32_t i = 0; i < npts; i++) {
+    LaunchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.prm = dp;
+    a.prm.seed_lo = (uint32_t)seed;
+    a.prm.seed_hi = (uint32_t)(seed >> 32);
+    a.npts = 1;
+    a.ncodes = 1;
+    a.codes[0] = pts[i].code->dev;
+    DevPoint &d = a.pts[0];
+    d.code = 0;
+    d.T = pts[i].tick_budget > 0 ? pts[i].tick_budget : prm->tick_budget;
+    d.shots = pts[i].shots;
+    d.shot0 = pts[i].shot0;
+    d.point_id = pts[i].point_id;
+    d.p_thr = prob_threshold(pts[i].p);
+    d.item0 = item0;
+    a.total_items = pts[i].shots;
+    a.slot_bytes = (uint32_t)plain_slot_bytes(a.codes[0], dp.prec);
+    a.slots = (uint8_t *)ws + kWsHeader;
+    a.rec = rec;
+    a.e_final = e_final;
+    a.e_final_words = words;
+    a.tally = tally + i;
+    item0 += pts[i].shots;
+    const int grid = (int)pts[i].shots;
+    if (grid == 0) continue;
+    int st = launch_plain(a, 0, 0, running, grid, pl.block, stream);
+    if (st) return st;
+    for (int t = 1; t <= d.T; t++) {
+      cudaError_t err = cudaMemsetAsync(running, 0, sizeof(int), s);
+      if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync");
+      st = launch_plain(a, 1, t, running, grid, pl.block, stream);
+      if (st) return st;
+      err = cudaMemcpyAsync(ctx->pinned, running, sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+      if (err != cudaSuccess) return cuda_fail(err, "plain path poll");
+      if (*ctx->pinned == 0) break;
+    }
+    st = launch_plain(a, 2, 0, running, grid, pl.block, stream);
+    if (st) return st;
+  }
+  return LIM_OK;
+}
+
 int upload_code(lim_ctx *ctx, HostCode &hc, lim_code **out) {
   lim_code *c = new (std::nothrow) lim_code();
   if (!c) return bad(LIM_E_NOMEM, "host allocation failed");
@@ -251,7 +325,7 @@ int upload_code(lim_ctx *ctx, HostCode &hc, lim_code **out) {
   const HostCode &h = c->host;
   const size_t nw = (h.n + 31) / 32;
   // every table starts on a 16-byte boundary (rows are read with vector loads)
-  const size_t words = (h.m + 1) + 3 * (size_t)h.E + (h.n + 1) + (size_t)h.k * nw + 6 * 4;
+  const size_t words = (h.m + 1) + 3 * (size_t)h.E + (h.n + 1) + (size_t)h.k * nw + h.partner.size() + 7 * 4;
   DevCode &d = c->dev;
   d.n = h.n;
   d.m = h.m;
@@ -261,6 +335,8 @@ int upload_code(lim_ctx *ctx, HostCode &hc, lim_code **out) {
   d.mw = (h.m + 31) / 32;
   d.dc_max = h.dc_max;
   d.dv_max = h.dv_max;
+  d.dv_u = h.dv_min == h.dv_max ? h.dv_max : 0;
+  d.dc_u = h.dc_min == h.dc_max ? h.dc_max : 0;
   // degree classes (see lim_device.cuh): exact when every node has that degree
   if (h.dv_min == h.dv_max && h.dv_max == 2) d.var_cls = 0;
   else if (h.dv_min == h.dv_max && h.dv_max == 3) d.var_cls = 1;
@@ -294,6 +370,7 @@ int upload_code(lim_ctx *ctx, HostCode &hc, lim_code **out) {
   };
   size_t o_cptr = put(h.c_ptr), o_cvar = put(h.c_var), o_vptr = put(h.v_ptr), o_vedge = put(h.v_edge),
          o_vchk = put(h.v_chk);
+  size_t o_part = put(h.partner);
   size_t o_lg = buf.size();
   for (uint32_t w : h.logicals) buf.push_back((int32_t)w);
   err = cudaMemcpy(c->dmem, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice);
@@ -309,6 +386,7 @@ int upload_code(lim_ctx *ctx, HostCode &hc, lim_code **out) {
   d.v_edge = base + o_vedge;
   d.v_chk = base + o_vchk;
   d.logicals = (const uint32_t *)(base + o_lg);
+  d.partner = h.partner.empty() ? nullptr : base + o_part;
   *out = c;
   return LIM_OK;
 }
@@ -364,6 +442,7 @@ int lim_ctx_create(int device, lim_ctx **out) {
 }
 
 int lim_ctx_destroy(lim_ctx *ctx) {
+  if (ctx && ctx->pinned) cudaFreeHost(ctx->pinned);
   delete ctx;
   return LIM_OK;
 }
@@ -499,6 +578,11 @@ int lim_run_batch(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_p
     st = make_plan(ctx, pts, npts, prm, dp, pl);
     if (st) return st;
     if (workspace_bytes < pl.workspace) return bad(LIM_E_NOMEM, "workspace too small");
+    if (pl.plain) {
+      cudaError_t err = cudaMemsetAsync(tally, 0, sizeof(lim_tally) * npts, (cudaStream_t)stream);
+      if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync");
+      return run_plain(ctx, pl, pts, npts, prm, dp, seed, workspace, rec, e_final, tally, stream);
+    }
     LaunchArgs a;
     fill_args(pl, pts, npts, prm, dp, seed, workspace, a);
     a.rec = rec;
@@ -526,6 +610,7 @@ int lim_trace(lim_ctx *ctx, const lim_code *code, const lim_params *prm, double 
     lim_point pt = {code, p, 1, shot, point_id, 0};
     if (pt.code->dev.m == 0) return bad(LIM_E_INVAL, "empty code");
     lim_params one = *prm;
+    if (one.variant == LIM_VARIANT_PLAIN) one.variant = LIM_VARIANT_CTA;  // traces come from the batch kernel
     Plan pl;
     st = make_plan(ctx, &pt, 1, &one, dp, pl);
     if (st) return st;
@@ -659,6 +744,7 @@ extern "C" int lim_run_batch_static(lim_ctx *ctx, const lim_point *pts, uint32_t
     Plan pl;
     st = make_plan(ctx, pts, npts, prm, dp, pl);
     if (st) return st;
+    if (pl.plain) return bad(LIM_E_UNSUPPORTED, "the plain baseline path needs a caller workspace");
     if (pl.workspace > kStaticWorkspaceBytes)
       return bad(LIM_E_NOMEM, "this batch needs more workspace than the 64 MiB static array; "
                               "use lim_run_batch with a caller buffer");

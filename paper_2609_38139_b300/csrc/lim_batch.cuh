@@ -1,7 +1,8 @@
-// lim_batch.cuh -- the persistent batch kernel: one team (a thread block or a
-// warp) runs one shot at a time from start to end, taking work items
-// (point, shot) from a device queue.  Included once per message precision by
-// lim_batch_*.cu so the instantiations compile in parallel.
+// lim_batch.cuh -- one shot of the inference machine as three team-level steps
+// (init, tick, finish), the persistent batch kernel that runs whole shots from a
+// device work queue, and the plain per-tick kernels of the baseline path.
+// Included once per message precision by lim_batch_*.cu so the instantiations
+// compile in parallel.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -13,6 +14,8 @@ namespace batch_detail {
 
 constexpr uint8_t kNone = 0, kPending = 1, kExec = 2, kSkip = 3;
 
+// Control block of one shot (shared memory in the persistent kernel, HBM in the
+// plain path).
 struct TeamCtl {
   unsigned long long item;
   int32_t ncand;    // candidate moves of the current tick
@@ -20,14 +23,15 @@ struct TeamCtl {
   int32_t moves;
   int32_t err;
   uint32_t logmask; // parities of e with the X-logicals
-  int32_t pad[9];
+  int32_t t_clr, converged, ticks, sweeps, vc_sel, done;
+  int32_t pad[3];
 };
 static_assert(sizeof(TeamCtl) == 64, "TeamCtl layout");
 
 LIM_HD inline size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct Layout {
-  // offsets inside the team's shared memory
+  // offsets inside the team's shared memory (or the plain path's HBM slot)
   uint32_t e, s, s0, sg, smem_free;
   // offsets inside the message block and the per-check scratch block
   uint32_t cv, vc0, vc1, msg_bytes;
@@ -63,6 +67,54 @@ __device__ __forceinline__ Layout layout(const DevCode &C, int prec) {
   return L;
 }
 
+// Pointers to one shot's state.
+template <class T>
+struct ShotView {
+  TeamCtl *ctl;
+  uint32_t *e, *s, *s0, *sg;
+  T *CV, *VC0, *VC1;
+  volatile uint8_t *cstate;
+  uint32_t *cprio;
+  int32_t *ctgt, *clist;
+};
+
+template <class T>
+__device__ __forceinline__ ShotView<T> make_view(const Layout &Ly, uint8_t *base, uint8_t *msg,
+                                                 uint8_t *chk) {
+  ShotView<T> V;
+  V.ctl = reinterpret_cast<TeamCtl *>(base);
+  V.e = reinterpret_cast<uint32_t *>(base + Ly.e);
+  V.s = reinterpret_cast<uint32_t *>(base + Ly.s);
+  V.s0 = reinterpret_cast<uint32_t *>(base + Ly.s0);
+  V.sg = reinterpret_cast<uint32_t *>(base + Ly.sg);
+  V.CV = reinterpret_cast<T *>(msg + Ly.cv);
+  V.VC0 = reinterpret_cast<T *>(msg + Ly.vc0);
+  V.VC1 = reinterpret_cast<T *>(msg + Ly.vc1);
+  V.cstate = chk + Ly.cstate;
+  V.cprio = reinterpret_cast<uint32_t *>(chk + Ly.cprio);
+  V.ctgt = reinterpret_cast<int32_t *>(chk + Ly.ctgt);
+  V.clist = reinterpret_cast<int32_t *>(chk + Ly.clist);
+  return V;
+}
+
+// Per-shot scalars carried from tick to tick.
+struct ShotRegs {
+  int32_t t_clr, converged, ticks, sweeps, vc_sel;
+};
+
+// Phase timer: rank 0 of the team adds the cycles since its last mark to the
+// point's counter (only when profiling is on; the marks sit after barriers).
+struct PhaseClock {
+  long long last;
+  int64_t *acc;  // lim_tally::phase_cycles of the point, or null
+  __device__ __forceinline__ void mark(int phase) {
+    if (!acc) return;
+    const long long now = clock64();
+    atomicAdd(reinterpret_cast<unsigned long long *>(acc + phase), (unsigned long long)(now - last));
+    last = now;
+  }
+};
+
 __device__ __forceinline__ int hist_bin(int t) {
   if (t <= 0) return 0;
   int b = 32 - __clz(t);  // t in [2^(b-1), 2^b)
@@ -77,41 +129,12 @@ __device__ __forceinline__ void write_trace(const Team &tm, const LaunchArgs &A,
   for (int w = tm.rank(); w < C.mw; w += tm.size()) A.trace_s[(size_t)row * C.mw + w] = s[w];
 }
 
-// One shot, start to end, by one team.
-template <class Team, int PREC, int RULE, int FB>
-__device__ void run_shot(const Team &tm, const LaunchArgs &A, int pidx, uint32_t shot,
-                         uint64_t item, uint8_t *tsm, uint8_t *gslot) {
-  using M = MT<PREC>;
-  using T = typename M::T;
-  using Acc = typename M::A;
+// --- init: noise and initial syndrome (Preliminaries), m = 0 (Algorithm 1) ----
+template <class Team, int PREC>
+__device__ void shot_init(const Team &tm, const LaunchArgs &A, const DevPoint &pt, const DevCode &C,
+                          uint32_t shot, const ShotView<typename MT<PREC>::T> &V, ShotRegs &R) {
+  using T = typename MT<PREC>::T;
   const DevParams &P = A.prm;
-  const DevPoint &pt = A.pts[pidx];
-  const DevCode &C = A.codes[pt.code];
-  const Layout Ly = layout(C, PREC);
-  TeamCtl *ctl = reinterpret_cast<TeamCtl *>(tsm);
-  uint32_t *e = reinterpret_cast<uint32_t *>(tsm + Ly.e);
-  uint32_t *s = reinterpret_cast<uint32_t *>(tsm + Ly.s);
-  uint32_t *s0 = reinterpret_cast<uint32_t *>(tsm + Ly.s0);
-  uint32_t *sg = reinterpret_cast<uint32_t *>(tsm + Ly.sg);
-  // Shared memory after the bit vectors holds the messages and/or the per-check
-  // scratch when they fit; the rest lives in this team's global slot, which is
-  // laid out as [messages][per-check scratch].
-  uint8_t *sfree = tsm + Ly.smem_free;
-  uint8_t *msg = pt.msg_smem ? sfree : gslot;
-  uint8_t *chk = pt.chk_smem ? (pt.msg_smem ? sfree + Ly.msg_bytes : sfree) : gslot + Ly.msg_bytes;
-  T *CV = reinterpret_cast<T *>(msg + Ly.cv);
-  T *VCc = reinterpret_cast<T *>(msg + Ly.vc0);
-  T *VCn = reinterpret_cast<T *>(msg + Ly.vc1);
-  volatile uint8_t *cstate = chk + Ly.cstate;
-  uint32_t *cprio = reinterpret_cast<uint32_t *>(chk + Ly.cprio);
-  int32_t *ctgt = reinterpret_cast<int32_t *>(chk + Ly.ctgt);
-  int32_t *clist = reinterpret_cast<int32_t *>(chk + Ly.clist);
-  const bool tracing = A.trace_e != nullptr;
-  const FlipCtx F{e, s, sg, &ctl->defects, &ctl->moves};
-  const bool frame_s0 = (FB == LIM_FB_BIT_DISCRETE) || P.gauge_on_move;
-  const uint32_t *seff = frame_s0 ? s0 : s;  // effective syndrome of the check half-sweep
-
-  // --- noise and initial syndrome (Preliminaries) -------------------------
   for (int w = tm.rank(); w < C.nw; w += tm.size()) {
     uint32_t word = 0;
 #pragma unroll 1
@@ -125,20 +148,21 @@ __device__ void run_shot(const Team &tm, const LaunchArgs &A, int pidx, uint32_t
       for (int b = 0; b < 4; b++)
         if (v0 + b < C.n && (uint64_t)uu[b] < pt.p_thr) word |= 1u << (4 * j + b);
     }
-    e[w] = word;
-    sg[w] = 0;
+    V.e[w] = word;
+    V.sg[w] = 0;
   }
   for (int i = tm.rank(); i < C.E; i += tm.size()) {
-    CV[i] = T(0);
-    VCc[i] = T(0);
+    V.CV[i] = T(0);
+    V.VC0[i] = T(0);
   }
-  for (int i = tm.rank(); i < C.m; i += tm.size()) cstate[i] = kNone;
+  for (int i = tm.rank(); i < C.m; i += tm.size()) V.cstate[i] = kNone;
   if (tm.rank() == 0) {
-    ctl->ncand = 0;
-    ctl->defects = 0;
-    ctl->moves = 0;
-    ctl->err = 0;
-    ctl->logmask = 0;
+    V.ctl->ncand = 0;
+    V.ctl->defects = 0;
+    V.ctl->moves = 0;
+    V.ctl->err = 0;
+    V.ctl->logmask = 0;
+    V.ctl->done = 0;
   }
   tm.sync();
   for (int w = tm.rank(); w < C.mw; w += tm.size()) {
@@ -149,203 +173,259 @@ __device__ void run_shot(const Team &tm, const LaunchArgs &A, int pidx, uint32_t
       int par = 0;
       for (int j = __ldg(C.c_ptr + c); j < __ldg(C.c_ptr + c + 1); j++) {
         const int v = __ldg(C.c_var + j);
-        par ^= (e[v >> 5] >> (v & 31)) & 1;
+        par ^= (V.e[v >> 5] >> (v & 31)) & 1;
       }
       word |= (uint32_t)par << b;
     }
-    s[w] = word;
-    s0[w] = word;
-    if (word) atomicAdd(&ctl->defects, __popc(word));
+    V.s[w] = word;
+    V.s0[w] = word;
+    if (word) atomicAdd(&V.ctl->defects, __popc(word));
   }
   tm.sync();
-  if (tracing) write_trace(tm, A, C, 0, e, s);
+  if (A.trace_e) write_trace(tm, A, C, 0, V.e, V.s);
+  R.t_clr = -1;
+  R.converged = 0;
+  R.ticks = 0;
+  R.sweeps = 0;
+  R.vc_sel = 0;
+  if (V.ctl->defects == 0) {
+    R.t_clr = 0;
+    R.converged = 1;
+  }
+}
 
-  int t_clr = -1, converged = 0, ticks = 0, sweeps = 0;
-  if (ctl->defects == 0) {
-    t_clr = 0;
-    converged = 1;
-  } else {
-    const Acc pi = prior<Acc>(P);
-    for (int t = 1; t <= pt.T; t++) {
-      ticks = t;
-      // --- read-out + feedback (+ the qubit half-sweep of sweep 1, which reads
-      //     the same messages and does not depend on the feedback) -----------
-      if (FB == LIM_FB_CHECK_MOVE) {
-        for (int w = tm.rank(); w < C.mw; w += tm.size()) {
-          uint32_t bits = s[w];
-          while (bits) {
-            const int c = 32 * w + __ffs(bits) - 1;
-            bits &= bits - 1;
-            const U4 u = philox4x32_10(shot, (uint32_t)t, (uint32_t)c, (pt.point_id << 4) | 1u,
-                                       P.seed_lo, P.seed_hi);
-            if ((uint64_t)u.x >= P.ring_thr) continue;  // this check's clock did not ring
-            if (P.gauge_on_move) {
-              const int idx = atomicAdd(&ctl->ncand, 1);
-              clist[idx] = c;
-              cprio[c] = u.y;
-              ctgt[c] = (int32_t)u.z;
-              continue;
-            }
-            // Evidence and LocalMove target from the beliefs of N(c) (Algorithm 1).
-            const int cb = __ldg(C.c_ptr + c), d = __ldg(C.c_ptr + c + 1) - cb;
-            Acc Lv[kMaxDeg];
-            Acc best = -inf_of(Acc(0));
+// --- one tick: read-out, feedback, termination test, K sweeps ------------------
+// Returns true when the shot has ended at this tick (syndrome cleared, or the
+// budget reached).  Every thread of the team returns the same value.
+template <class Team, int PREC, int RULE, int FB>
+__device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &pt, const DevCode &C,
+                          uint32_t shot, int t, const ShotView<typename MT<PREC>::T> &V, ShotRegs &R,
+                          PhaseClock &clk) {
+  using M = MT<PREC>;
+  using T = typename M::T;
+  using Acc = typename M::A;
+  const DevParams &P = A.prm;
+  TeamCtl *ctl = V.ctl;
+  // Fused mode (alpha = 1, uniform qubit degree, check-centric rule): the three
+  // message buffers rotate as check->qubit messages of sweeps k, k-1, k-2 and the
+  // qubit->check messages are never stored; vc_sel counts the rotation.
+  const bool fused = FB == LIM_FB_CHECK_MOVE && P.alpha_is_one && fused_ok(C);
+  T *const B[3] = {V.CV, V.VC0, V.VC1};
+  T *CV = fused ? B[R.vc_sel] : V.CV;
+  T *VCc = R.vc_sel ? V.VC1 : V.VC0;
+  T *VCn = R.vc_sel ? V.VC0 : V.VC1;
+  const FlipCtx F{V.e, V.s, V.sg, &ctl->defects, &ctl->moves};
+  const bool frame_s0 = (FB == LIM_FB_BIT_DISCRETE) || P.gauge_on_move;
+  const uint32_t *seff = frame_s0 ? V.s0 : V.s;  // effective syndrome of the check half-sweep
+  R.ticks = t;
+  // --- read-out + feedback (+ the qubit half-sweep of sweep 1, which reads the
+  //     same messages and does not depend on the feedback) --------------------
+  if (FB == LIM_FB_CHECK_MOVE) {
+    for (int w = tm.rank(); w < C.mw; w += tm.size()) {
+      uint32_t bits = V.s[w];
+      while (bits) {
+        const int c = 32 * w + __ffs(bits) - 1;
+        bits &= bits - 1;
+        const U4 u = philox4x32_10(shot, (uint32_t)t, (uint32_t)c, (pt.point_id << 4) | 1u,
+                                   P.seed_lo, P.seed_hi);
+        if ((uint64_t)u.x >= P.ring_thr) continue;  // this check's clock did not ring
+        if (P.gauge_on_move) {
+          const int idx = atomicAdd(&ctl->ncand, 1);
+          V.clist[idx] = c;
+          V.cprio[c] = u.y;
+          V.ctgt[c] = (int32_t)u.z;
+          continue;
+        }
+        // Evidence and LocalMove target from the beliefs of N(c) (Algorithm 1).
+        const int cb = __ldg(C.c_ptr + c), d = __ldg(C.c_ptr + c + 1) - cb;
+        Acc Lv[kMaxDeg];
+        Acc best = -inf_of(Acc(0));
 #pragma unroll
-            for (int j = 0; j < kMaxDeg; j++) {
-              if (j < d) {
-                Lv[j] = belief<PREC>(C, P, __ldg(C.c_var + cb + j), CV);
-                if (Lv[j] > best) best = Lv[j];
-              }
-            }
-            if (!evidence(P, best, d)) continue;
-            int nt = 0;
-#pragma unroll
-            for (int j = 0; j < kMaxDeg; j++)
-              if (j < d && Lv[j] == best) nt++;
-            int pick = (int)(((uint64_t)u.z * (uint64_t)nt) >> 32);
-            int vstar = -1;
-#pragma unroll
-            for (int j = 0; j < kMaxDeg; j++) {
-              if (j < d && Lv[j] == best) {
-                if (pick == 0 && vstar < 0) vstar = __ldg(C.c_var + cb + j);
-                pick--;
-              }
-            }
-            const int idx = atomicAdd(&ctl->ncand, 1);
-            clist[idx] = c;
-            cprio[c] = u.y;
-            ctgt[c] = vstar;
-            cstate[c] = kPending;
+        for (int j = 0; j < kMaxDeg; j++) {
+          if (j < d) {
+            Lv[j] = belief<PREC>(C, P, __ldg(C.c_var + cb + j), CV);
+            if (Lv[j] > best) best = Lv[j];
           }
         }
-        if (t < pt.T) var_pass<PREC, false>(tm.rank(), tm.size(), C, P, CV, VCc, VCn, F);
-      } else {
-        // Bit-centric rule, Eq. 3-4: f_v = 1[L_v > 0]; the gauge switch of Sec. S2
-        // is a toggle of sigma_v (the stored messages stay as they are).
-        var_pass<PREC, true>(tm.rank(), tm.size(), C, P, CV, VCc, VCn, F);
+        if (!evidence(P, best, d)) continue;
+        int nt = 0;
+#pragma unroll
+        for (int j = 0; j < kMaxDeg; j++)
+          if (j < d && Lv[j] == best) nt++;
+        int pick = (int)(((uint64_t)u.z * (uint64_t)nt) >> 32);
+        int vstar = -1;
+#pragma unroll
+        for (int j = 0; j < kMaxDeg; j++) {
+          if (j < d && Lv[j] == best) {
+            if (pick == 0 && vstar < 0) vstar = __ldg(C.c_var + cb + j);
+            pick--;
+          }
+        }
+        const int idx = atomicAdd(&ctl->ncand, 1);
+        V.clist[idx] = c;
+        V.cprio[c] = u.y;
+        V.ctgt[c] = vstar;
+        V.cstate[c] = kPending;
       }
-      tm.sync();
-      if (FB == LIM_FB_CHECK_MOVE) {
-        const int nc = ctl->ncand;
-        if (nc > 0) {
-          if (!P.gauge_on_move) {
-            // Sequential semantics of the rings in priority order, resolved in
-            // parallel: candidate c acts iff it is still active at its turn, i.e.
-            // iff an even number of earlier-priority executed moves flipped a
-            // qubit of N(c).  Each round settles every candidate whose earlier
-            // neighbours are settled; the earliest pending one always settles.
-            for (int round = 0;; round++) {
-              int pend = 0;
-              for (int j = tm.rank(); j < nc; j += tm.size()) {
-                const int c = clist[j];
-                if (cstate[c] != kPending) continue;
-                const uint32_t pc = cprio[c];
-                const int cb = __ldg(C.c_ptr + c), ce = __ldg(C.c_ptr + c + 1);
-                int ready = 1, active = 1;
-                for (int jj = cb; jj < ce && ready; jj++) {
-                  const int u = __ldg(C.c_var + jj);
-                  for (int q = __ldg(C.v_ptr + u); q < __ldg(C.v_ptr + u + 1); q++) {
-                    const int c2 = __ldg(C.v_chk + q);
-                    if (c2 == c) continue;
-                    const uint8_t st2 = cstate[c2];
-                    if (st2 == kNone || ctgt[c2] != u) continue;
-                    const uint32_t p2 = cprio[c2];
-                    if (p2 < pc || (p2 == pc && c2 < c)) {
-                      if (st2 == kPending) ready = 0;
-                      else if (st2 == kExec) active ^= 1;
-                    }
-                  }
+    }
+    if (t < pt.T && !fused) var_pass<PREC, false>(tm.rank(), tm.size(), C, P, CV, VCc, VCn, F);
+  } else {
+    // Bit-centric rule, Eq. 3-4: f_v = 1[L_v > 0]; the gauge switch of Sec. S2
+    // is a toggle of sigma_v (the stored messages stay as they are).
+    var_pass<PREC, true>(tm.rank(), tm.size(), C, P, CV, VCc, VCn, F);
+  }
+  tm.sync();
+  clk.mark(1);
+  if (FB == LIM_FB_CHECK_MOVE) {
+    const int nc = ctl->ncand;
+    if (nc > 0) {
+      if (!P.gauge_on_move) {
+        // Sequential semantics of the rings in priority order, resolved in
+        // parallel: candidate c acts iff it is still active at its turn, i.e. iff
+        // an even number of earlier-priority executed moves flipped a qubit of
+        // N(c).  Each round settles every candidate whose earlier neighbours are
+        // settled; the earliest pending one always settles.
+        for (int round = 0;; round++) {
+          int pend = 0;
+          for (int j = tm.rank(); j < nc; j += tm.size()) {
+            const int c = V.clist[j];
+            if (V.cstate[c] != kPending) continue;
+            const uint32_t pc = V.cprio[c];
+            const int cb = __ldg(C.c_ptr + c), ce = __ldg(C.c_ptr + c + 1);
+            int ready = 1, active = 1;
+            for (int jj = cb; jj < ce && ready; jj++) {
+              const int u = __ldg(C.c_var + jj);
+              for (int q = __ldg(C.v_ptr + u); q < __ldg(C.v_ptr + u + 1); q++) {
+                const int c2 = __ldg(C.v_chk + q);
+                if (c2 == c) continue;
+                const uint8_t st2 = V.cstate[c2];
+                if (st2 == kNone || V.ctgt[c2] != u) continue;
+                const uint32_t p2 = V.cprio[c2];
+                if (p2 < pc || (p2 == pc && c2 < c)) {
+                  if (st2 == kPending) ready = 0;
+                  else if (st2 == kExec) active ^= 1;
                 }
-                if (ready) cstate[c] = active ? kExec : kSkip;
-                else pend = 1;
               }
-              if (!tm.any(pend)) break;
-              if (round > nc + 2) {  // cannot happen: priorities are a total order
-                if (tm.rank() == 0) ctl->err = 1;
+            }
+            if (ready) V.cstate[c] = active ? kExec : kSkip;
+            else pend = 1;
+          }
+          if (!tm.any(pend)) break;
+          if (round > nc + 2) {  // cannot happen: priorities are a total order
+            if (tm.rank() == 0) ctl->err = 1;
+            break;
+          }
+        }
+        for (int j = tm.rank(); j < nc; j += tm.size()) {
+          const int c = V.clist[j];
+          if (V.cstate[c] == kExec) flip_bits(C, F, V.ctgt[c]);
+          V.cstate[c] = kNone;
+        }
+      } else if (tm.rank() == 0) {
+        // With the gauge switch on every move, a flip changes later beliefs:
+        // process the rings one by one in priority order.
+        int32_t *clist = V.clist;
+        const uint32_t *cprio = V.cprio;
+        for (int i = 1; i < nc; i++) {
+          const int c = clist[i];
+          int j = i - 1;
+          while (j >= 0 && (cprio[clist[j]] > cprio[c] ||
+                            (cprio[clist[j]] == cprio[c] && clist[j] > c))) {
+            clist[j + 1] = clist[j];
+            j--;
+          }
+          clist[j + 1] = c;
+        }
+        for (int i = 0; i < nc; i++) {
+          const int c = clist[i];
+          if (!((V.s[c >> 5] >> (c & 31)) & 1)) continue;
+          const int cb = __ldg(C.c_ptr + c), d = __ldg(C.c_ptr + c + 1) - cb;
+          Acc Lv[kMaxDeg];
+          Acc best = -inf_of(Acc(0));
+          for (int j = 0; j < d; j++) {
+            const int v = __ldg(C.c_var + cb + j);
+            const Acc Ls = belief<PREC>(C, P, v, CV);
+            Lv[j] = ((V.sg[v >> 5] >> (v & 31)) & 1) ? -Ls : Ls;
+            if (Lv[j] > best) best = Lv[j];
+          }
+          if (!evidence(P, best, d)) continue;
+          int nt = 0;
+          for (int j = 0; j < d; j++)
+            if (Lv[j] == best) nt++;
+          int pick = (int)(((uint64_t)(uint32_t)V.ctgt[c] * (uint64_t)nt) >> 32);
+          int vstar = -1;
+          for (int j = 0; j < d; j++)
+            if (Lv[j] == best) {
+              if (pick == 0) {
+                vstar = __ldg(C.c_var + cb + j);
                 break;
               }
+              pick--;
             }
-            for (int j = tm.rank(); j < nc; j += tm.size()) {
-              const int c = clist[j];
-              if (cstate[c] == kExec) flip_bits(C, F, ctgt[c]);
-              cstate[c] = kNone;
-            }
-          } else if (tm.rank() == 0) {
-            // With the gauge switch on every move, a flip changes later beliefs:
-            // process the rings one by one in priority order.
-            for (int i = 1; i < nc; i++) {
-              const int c = clist[i];
-              int j = i - 1;
-              while (j >= 0 && (cprio[clist[j]] > cprio[c] ||
-                                (cprio[clist[j]] == cprio[c] && clist[j] > c))) {
-                clist[j + 1] = clist[j];
-                j--;
-              }
-              clist[j + 1] = c;
-            }
-            for (int i = 0; i < nc; i++) {
-              const int c = clist[i];
-              if (!((s[c >> 5] >> (c & 31)) & 1)) continue;
-              const int cb = __ldg(C.c_ptr + c), d = __ldg(C.c_ptr + c + 1) - cb;
-              Acc Lv[kMaxDeg];
-              Acc best = -inf_of(Acc(0));
-              for (int j = 0; j < d; j++) {
-                const int v = __ldg(C.c_var + cb + j);
-                const Acc Ls = belief<PREC>(C, P, v, CV);
-                Lv[j] = ((sg[v >> 5] >> (v & 31)) & 1) ? -Ls : Ls;
-                if (Lv[j] > best) best = Lv[j];
-              }
-              if (!evidence(P, best, d)) continue;
-              int nt = 0;
-              for (int j = 0; j < d; j++)
-                if (Lv[j] == best) nt++;
-              int pick = (int)(((uint64_t)(uint32_t)ctgt[c] * (uint64_t)nt) >> 32);
-              int vstar = -1;
-              for (int j = 0; j < d; j++)
-                if (Lv[j] == best) {
-                  if (pick == 0) {
-                    vstar = __ldg(C.c_var + cb + j);
-                    break;
-                  }
-                  pick--;
-                }
-              flip_bits(C, F, vstar);
-              sg[vstar >> 5] ^= 1u << (vstar & 31);
-            }
-          }
-          tm.sync();
-          if (tm.rank() == 0) ctl->ncand = 0;
+          flip_bits(C, F, vstar);
+          V.sg[vstar >> 5] ^= 1u << (vstar & 31);
         }
       }
-      if (tracing) write_trace(tm, A, C, t, e, s);
-      if (ctl->defects == 0) {  // clearance time
-        t_clr = t;
-        converged = 1;
-        break;
-      }
-      if (t == pt.T) break;
-      // --- check half-sweep of sweep 1, then sweeps 2..K -------------------
-      for (int k = 0; k < P.K; k++) {
-        if (k > 0) {
-          var_pass<PREC, false>(tm.rank(), tm.size(), C, P, CV, VCc, VCn, F);
-          tm.sync();
-        }
-        check_pass<PREC, RULE>(tm.rank(), tm.size(), C, P, SBitWords{seff}, VCc, CV);
-        tm.sync();
-        T *tmp = VCc;
-        VCc = VCn;
-        VCn = tmp;
-        sweeps++;
-      }
-      (void)pi;
+      tm.sync();
+      if (tm.rank() == 0) ctl->ncand = 0;
     }
   }
-  // --- logical check (decoding criteria (1)-(2)) ----------------------------
+  clk.mark(2);
+  if (A.trace_e) write_trace(tm, A, C, t, V.e, V.s);
+  if (ctl->defects == 0) {  // clearance time
+    R.t_clr = t;
+    R.converged = 1;
+    return true;
+  }
+  if (t == pt.T) return true;
+  // --- check half-sweep of sweep 1, then sweeps 2..K ---------------------------
+  if (fused) {
+    for (int k = 0; k < P.K; k++) {
+      // The very first sweep maps m = 0 to CV = 0 (every check has degree >= 2),
+      // which the zeroed second buffer already holds.
+      if (R.sweeps > 0) {
+        if (pt.msg_smem)
+          fused_pass<PREC, RULE, true>(tm.rank(), tm.size(), C, P, SBitWords{seff},
+                                       B[(R.vc_sel + 2) % 3], B[(R.vc_sel + 1) % 3]);
+        else
+          fused_pass<PREC, RULE, false>(tm.rank(), tm.size(), C, P, SBitWords{seff},
+                                        B[(R.vc_sel + 2) % 3], B[(R.vc_sel + 1) % 3]);
+      }
+      tm.sync();
+      clk.mark(k == 0 ? 3 : 4);
+      R.vc_sel = (R.vc_sel + 1) % 3;
+      R.sweeps++;
+    }
+    return false;
+  }
+  for (int k = 0; k < P.K; k++) {
+    if (k > 0) {
+      var_pass<PREC, false>(tm.rank(), tm.size(), C, P, CV, VCc, VCn, F);
+      tm.sync();
+    }
+    check_pass<PREC, RULE>(tm.rank(), tm.size(), C, P, SBitWords{seff}, VCc, CV);
+    tm.sync();
+    clk.mark(k == 0 ? 3 : 4);
+    T *tmp = VCc;
+    VCc = VCn;
+    VCn = tmp;
+    R.vc_sel ^= 1;
+    R.sweeps++;
+  }
+  return false;
+}
+
+// --- finish: logical check (decoding criteria (1)-(2)), record, tally ----------
+template <class Team, int PREC>
+__device__ void shot_finish(const Team &tm, const LaunchArgs &A, int pidx, const DevCode &C,
+                            uint64_t item, const ShotView<typename MT<PREC>::T> &V,
+                            const ShotRegs &R) {
+  TeamCtl *ctl = V.ctl;
   int failed = 1;
-  if (converged) {
+  if (R.converged) {
     uint32_t mask = 0;
     for (int w = tm.rank(); w < C.nw; w += tm.size()) {
-      const uint32_t ew = e[w];
+      const uint32_t ew = V.e[w];
       for (int j = 0; j < C.k; j++)
         if (__popc(ew & __ldg(C.logicals + (size_t)j * C.nw + w)) & 1) mask ^= 1u << j;
     }
@@ -353,20 +433,20 @@ __device__ void run_shot(const Team &tm, const LaunchArgs &A, int pidx, uint32_t
     tm.sync();
     failed = ctl->logmask != 0;
   }
-  if (tracing)
-    for (int row = ticks + 1; row <= A.trace_ticks; row++) write_trace(tm, A, C, row, e, s);
+  if (A.trace_e)
+    for (int row = R.ticks + 1; row <= A.trace_ticks; row++) write_trace(tm, A, C, row, V.e, V.s);
   if (A.e_final)
     for (int w = tm.rank(); w < C.nw; w += tm.size())
-      A.e_final[item * (uint64_t)A.e_final_words + w] = e[w];
+      A.e_final[item * (uint64_t)A.e_final_words + w] = V.e[w];
   if (tm.rank() == 0) {
     if (A.rec) {
       lim_shot_record r;
-      r.t_clr = t_clr;
-      r.converged = converged;
+      r.t_clr = R.t_clr;
+      r.converged = R.converged;
       r.failed = failed;
       r.moves = ctl->moves;
-      r.ticks = ticks;
-      r.sweeps = sweeps;
+      r.ticks = R.ticks;
+      r.sweeps = R.sweeps;
       A.rec[item] = r;
     }
     lim_tally *ty = A.tally + pidx;
@@ -375,23 +455,34 @@ __device__ void run_shot(const Team &tm, const LaunchArgs &A, int pidx, uint32_t
     };
     add(&ty->shots, 1);
     add(&ty->failures, failed);
-    add(&ty->nonconverged, !converged);
-    if (converged) {
-      add(&ty->sum_t, t_clr);
-      add(&ty->sum_t2, (long long)t_clr * t_clr);
-      add(&ty->hist[hist_bin(t_clr)], 1);
+    add(&ty->nonconverged, !R.converged);
+    if (R.converged) {
+      add(&ty->sum_t, R.t_clr);
+      add(&ty->sum_t2, (long long)R.t_clr * R.t_clr);
+      add(&ty->hist[hist_bin(R.t_clr)], 1);
     }
     add(&ty->moves, ctl->moves);
-    add(&ty->ticks, ticks);
-    add(&ty->sweeps, sweeps);
-    add(&ty->msg_updates, (long long)sweeps * 2 * C.E);
+    add(&ty->ticks, R.ticks);
+    add(&ty->sweeps, R.sweeps);
+    add(&ty->msg_updates, (long long)R.sweeps * 2 * C.E);
     if (ctl->err) add(&ty->errors, 1);
   }
   tm.sync();
 }
 
+__device__ __forceinline__ int find_point(const LaunchArgs &A, uint64_t item) {
+  int pidx = 0;
+  while (pidx + 1 < A.npts && A.pts[pidx + 1].item0 <= item) pidx++;
+  return pidx;
+}
+
+// --- the persistent kernel: every team takes shots from the queue and runs each
+//     one to the end; shared memory after the bit vectors holds the messages
+//     and/or the per-check scratch when they fit, the rest lives in this team's
+//     global slot, laid out as [messages][per-check scratch] ------------------
 template <class Team, int PREC, int RULE, int FB>
 __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ LaunchArgs A) {
+  using T = typename MT<PREC>::T;
   extern __shared__ __align__(16) uint8_t smem[];
   const Team tm;
   uint8_t *tsm = smem + (size_t)tm.local_index() * A.team_smem;
@@ -404,11 +495,90 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ Lau
     const uint64_t item = ctl->item;
     tm.sync();
     if (item >= A.total_items) break;
-    int pidx = 0;
-    while (pidx + 1 < A.npts && A.pts[pidx + 1].item0 <= item) pidx++;
-    const uint32_t shot = A.pts[pidx].shot0 + (uint32_t)(item - A.pts[pidx].item0);
-    run_shot<Team, PREC, RULE, FB>(tm, A, pidx, shot, item, tsm, gslot);
+    const int pidx = find_point(A, item);
+    const DevPoint &pt = A.pts[pidx];
+    const DevCode &C = A.codes[pt.code];
+    const uint32_t shot = pt.shot0 + (uint32_t)(item - pt.item0);
+    const Layout Ly = layout(C, PREC);
+    uint8_t *sfree = tsm + Ly.smem_free;
+    uint8_t *msg = pt.msg_smem ? sfree : gslot;
+    uint8_t *chk = pt.chk_smem ? (pt.msg_smem ? sfree + Ly.msg_bytes : sfree) : gslot + Ly.msg_bytes;
+    const ShotView<T> V = make_view<T>(Ly, tsm, msg, chk);
+    ShotRegs R;
+    PhaseClock clk{clock64(), (A.prm.profile && tm.rank() == 0) ? A.tally[pidx].phase_cycles : nullptr};
+    shot_init<Team, PREC>(tm, A, pt, C, shot, V, R);
+    clk.mark(0);
+    if (!R.converged)
+      for (int t = 1; t <= pt.T; t++)
+        if (shot_tick<Team, PREC, RULE, FB>(tm, A, pt, C, shot, t, V, R, clk)) break;
+    shot_finish<Team, PREC>(tm, A, pidx, C, item, V, R);
+    clk.mark(5);
   }
+}
+
+// --- the plain baseline: one launch per tick, one block per shot, every array
+//     of the shot in its HBM slot [control + bits][messages][per-check scratch] -
+template <int PREC>
+__device__ __forceinline__ ShotView<typename MT<PREC>::T> plain_view(const LaunchArgs &A,
+                                                                    const DevCode &C) {
+  const Layout Ly = layout(C, PREC);
+  uint8_t *slot = A.slots + (size_t)blockIdx.x * A.slot_bytes;
+  return make_view<typename MT<PREC>::T>(Ly, slot, slot + Ly.smem_free,
+                                         slot + Ly.smem_free + Ly.msg_bytes);
+}
+
+__device__ __forceinline__ void store_regs(TeamCtl *ctl, const ShotRegs &R) {
+  ctl->t_clr = R.t_clr;
+  ctl->converged = R.converged;
+  ctl->ticks = R.ticks;
+  ctl->sweeps = R.sweeps;
+  ctl->vc_sel = R.vc_sel;
+}
+
+__device__ __forceinline__ ShotRegs load_regs(const TeamCtl *ctl) {
+  return ShotRegs{ctl->t_clr, ctl->converged, ctl->ticks, ctl->sweeps, ctl->vc_sel};
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(1024) plain_init_kernel(const __grid_constant__ LaunchArgs A) {
+  const TeamCTA tm;
+  const DevPoint &pt = A.pts[0];
+  const DevCode &C = A.codes[pt.code];
+  const auto V = plain_view<PREC>(A, C);
+  ShotRegs R;
+  shot_init<TeamCTA, PREC>(tm, A, pt, C, pt.shot0 + blockIdx.x, V, R);
+  if (tm.rank() == 0) {
+    store_regs(V.ctl, R);
+    V.ctl->done = R.converged;
+  }
+}
+
+template <int PREC, int RULE, int FB>
+__global__ void __launch_bounds__(1024) plain_tick_kernel(const __grid_constant__ LaunchArgs A,
+                                                          int t, int *running) {
+  const TeamCTA tm;
+  const DevPoint &pt = A.pts[0];
+  const DevCode &C = A.codes[pt.code];
+  const auto V = plain_view<PREC>(A, C);
+  if (V.ctl->done) return;  // written by an earlier launch: uniform across the block
+  ShotRegs R = load_regs(V.ctl);
+  PhaseClock clk{clock64(), nullptr};
+  const bool end = shot_tick<TeamCTA, PREC, RULE, FB>(tm, A, pt, C, pt.shot0 + blockIdx.x, t, V, R, clk);
+  if (tm.rank() == 0) {
+    store_regs(V.ctl, R);
+    if (end) V.ctl->done = 1;
+    else atomicAdd(running, 1);
+  }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(1024) plain_finish_kernel(const __grid_constant__ LaunchArgs A) {
+  const TeamCTA tm;
+  const DevPoint &pt = A.pts[0];
+  const DevCode &C = A.codes[pt.code];
+  const auto V = plain_view<PREC>(A, C);
+  const ShotRegs R = load_regs(V.ctl);
+  shot_finish<TeamCTA, PREC>(tm, A, 0, C, pt.item0 + blockIdx.x, V, R);
 }
 
 template <class Team, int PREC>
@@ -423,8 +593,20 @@ const void *pick_kernel(int rule, int fb) {
              : (const void *)batch_kernel<Team, PREC, LIM_RULE_MINSUM, LIM_FB_BIT_DISCRETE>;
 }
 
-
-
+// The three plain kernels for (rule, feedback): init, tick, finish.
+template <int PREC>
+void pick_plain(int rule, int fb, const void **init, const void **tick, const void **finish) {
+  *init = (const void *)plain_init_kernel<PREC>;
+  *finish = (const void *)plain_finish_kernel<PREC>;
+  if (rule == LIM_RULE_SUMPRODUCT && !MT<PREC>::is_int)
+    *tick = fb == LIM_FB_CHECK_MOVE
+                ? (const void *)plain_tick_kernel<PREC, LIM_RULE_SUMPRODUCT, LIM_FB_CHECK_MOVE>
+                : (const void *)plain_tick_kernel<PREC, LIM_RULE_SUMPRODUCT, LIM_FB_BIT_DISCRETE>;
+  else
+    *tick = fb == LIM_FB_CHECK_MOVE
+                ? (const void *)plain_tick_kernel<PREC, LIM_RULE_MINSUM, LIM_FB_CHECK_MOVE>
+                : (const void *)plain_tick_kernel<PREC, LIM_RULE_MINSUM, LIM_FB_BIT_DISCRETE>;
+}
 
 }  // namespace batch_detail
 }  // namespace lim

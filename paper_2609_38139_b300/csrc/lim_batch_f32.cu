@@ -8,4 +8,9 @@ const void *batch_fn_f32(int warp, int rule, int fb) {
   return warp ? pick_kernel<TeamWarp, LIM_PREC_F32>(rule, fb) : pick_kernel<TeamCTA, LIM_PREC_F32>(rule, fb);
 }
 
+// The plain baseline path exists for binary32 messages only.
+void plain_fns_f32(int rule, int fb, const void **init, const void **tick, const void **finish) {
+  batch_detail::pick_plain<LIM_PREC_F32>(rule, fb, init, tick, finish);
+}
+
 }  // namespace lim

@@ -173,6 +173,20 @@ void finish(HostCode &hc) {
     hc.dv_max = std::max(hc.dv_max, d);
   }
   if (m == 0) hc.dc_min = 0;
+  // For uniform degrees: for every edge (c, v), the other edges of v in
+  // ascending check order -- the terms of v's message to c in Eq. 1.
+  hc.partner.clear();
+  if (hc.dv_min == hc.dv_max && hc.dv_max >= 2 && hc.dc_min == hc.dc_max && hc.dc_max >= 2) {
+    const int dv = hc.dv_max;
+    hc.partner.assign((size_t)hc.E * (dv - 1), 0);
+    for (int v = 0; v < n; v++)
+      for (int j = 0; j < dv; j++) {
+        const int e = hc.v_edge[hc.v_ptr[v] + j];
+        int o = 0;
+        for (int jj = 0; jj < dv; jj++)
+          if (jj != j) hc.partner[(size_t)e * (dv - 1) + o++] = hc.v_edge[hc.v_ptr[v] + jj];
+      }
+  }
 }
 
 int validate_csr(int32_t rows, int32_t n, const int32_t *ptr, const int32_t *col, const char *what) {

@@ -283,11 +283,13 @@ __device__ __forceinline__ void var_loop(int rank, int size, const DevCode &C, c
                                          const typename MT<PREC>::T *VCc, typename MT<PREC>::T *VCn,
                                          const FlipCtx &F) {
   int v = rank;
-  for (; v + size < C.n; v += 2 * size) {  // two qubits per iteration: independent loads overlap
+  for (; v + 3 * size < C.n; v += 4 * size) {  // four qubits per iteration: loads overlap
     var_one<PREC, DV, EXACT, READOUT>(C, P, v, CV, VCc, VCn, F);
     var_one<PREC, DV, EXACT, READOUT>(C, P, v + size, CV, VCc, VCn, F);
+    var_one<PREC, DV, EXACT, READOUT>(C, P, v + 2 * size, CV, VCc, VCn, F);
+    var_one<PREC, DV, EXACT, READOUT>(C, P, v + 3 * size, CV, VCc, VCn, F);
   }
-  if (v < C.n) var_one<PREC, DV, EXACT, READOUT>(C, P, v, CV, VCc, VCn, F);
+  for (; v < C.n; v += size) var_one<PREC, DV, EXACT, READOUT>(C, P, v, CV, VCc, VCn, F);
 }
 
 // The qubit half-sweep over all qubits of the code.
@@ -412,11 +414,13 @@ __device__ __forceinline__ void check_loop(int rank, int size, const DevCode &C,
                                            const SBit &sbit, const typename MT<PREC>::T *VCc,
                                            typename MT<PREC>::T *CV) {
   int c = rank;
-  for (; c + size < C.m; c += 2 * size) {
+  for (; c + 3 * size < C.m; c += 4 * size) {
     check_one<PREC, RULE, DC, EXACT>(C, P, c, sbit(c), VCc, CV);
     check_one<PREC, RULE, DC, EXACT>(C, P, c + size, sbit(c + size), VCc, CV);
+    check_one<PREC, RULE, DC, EXACT>(C, P, c + 2 * size, sbit(c + 2 * size), VCc, CV);
+    check_one<PREC, RULE, DC, EXACT>(C, P, c + 3 * size, sbit(c + 3 * size), VCc, CV);
   }
-  if (c < C.m) check_one<PREC, RULE, DC, EXACT>(C, P, c, sbit(c), VCc, CV);
+  for (; c < C.m; c += size) check_one<PREC, RULE, DC, EXACT>(C, P, c, sbit(c), VCc, CV);
 }
 
 // The check half-sweep over all checks; sbit(c) returns s~_c.
@@ -432,6 +436,161 @@ __device__ __noinline__ void check_pass(int rank, int size, const DevCode &C, co
     case kChkLe6: check_loop<PREC, RULE, 6, false>(rank, size, C, P, sbit, VCc, CV); break;
     default: check_loop<PREC, RULE, 8, false>(rank, size, C, P, sbit, VCc, CV); break;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Fused sweep for alpha = 1 and a uniform qubit degree DV.  Without relaxation
+// the qubit->check messages of Eq. 1 are a function of the previous check->qubit
+// messages only, VC_{k-1}[v->c] = clamp(pi + sum_{c' in N(v)\c} CV_{k-2}[c'->v]),
+// so they need not be stored: the check half-sweep computes them on the fly from
+// the partner edges of each of its edges, in the same order and with the same
+// storage rounding as the stored path, so the values are identical.  Check
+// messages live in three rotating buffers (k-2 read, k-1 read-out, k written).
+// ---------------------------------------------------------------------------
+template <int PREC>
+__device__ __forceinline__ typename MT<PREC>::A round_to_storage(typename MT<PREC>::A v) {
+  typename MT<PREC>::T t;
+  MT<PREC>::st(&t, v);
+  return MT<PREC>::ld(&t);
+}
+
+// Gathers of one check: its partner edges and the messages there.
+template <int PREC, int DC, int DV>
+struct FusedIn {
+  typename MT<PREC>::A in[DC * (DV - 1)];
+};
+
+template <int PREC, int DC, int DV>
+__device__ __forceinline__ void fused_gather(const DevCode &C, int c,
+                                             const typename MT<PREC>::T *__restrict__ CVp,
+                                             FusedIn<PREC, DC, DV> &g) {
+  constexpr int NP = DC * (DV - 1);
+  int pe[NP];
+  RowIO<int, NP>::load(C.partner + (size_t)c * NP, pe);
+#pragma unroll
+  for (int i = 0; i < NP; i++) g.in[i] = MT<PREC>::ld(CVp + pe[i]);
+}
+
+template <int PREC, int RULE, int DC, int DV>
+__device__ __forceinline__ void fused_compute(const DevCode &C, const DevParams &P, int c, int sbit,
+                                              const FusedIn<PREC, DC, DV> &g,
+                                              typename MT<PREC>::T *__restrict__ CVn) {
+  using M = MT<PREC>;
+  using T = typename M::T;
+  using A = typename M::A;
+  const A pi = prior<A>(P);
+  A x[DC];
+#pragma unroll
+  for (int j = 0; j < DC; j++) {
+    A acc = pi;
+#pragma unroll
+    for (int jj = 0; jj < DV - 1; jj++) acc = wadd(acc, g.in[j * (DV - 1) + jj]);
+    x[j] = round_to_storage<PREC>(update(P, A(0), acc));
+  }
+  A out[DC];
+  if (RULE == LIM_RULE_MINSUM || M::is_int) {
+    int neg = (sbit + DC) & 1;
+    A min1 = inf_of(A(0)), min2 = inf_of(A(0));
+    int imin = -1;
+#pragma unroll
+    for (int j = 0; j < DC; j++) {
+      const A a = absw(x[j]);
+      neg ^= (x[j] < A(0));
+      if (a < min1) {
+        min2 = min1;
+        min1 = a;
+        imin = j;
+      } else if (a < min2) {
+        min2 = a;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < DC; j++) {
+      const A mag = (j == imin) ? min2 : min1;
+      const bool ng = neg ^ (x[j] < A(0));
+      out[j] = (mag == A(0)) ? A(0) : (ng ? -mag : mag);
+    }
+  } else {
+    if constexpr (!M::is_int) {
+      float pre[DC], suf[DC];
+#pragma unroll
+      for (int j = 0; j < DC; j++) pre[j] = (j == 0) ? x[0] : boxplus(pre[j - 1], x[j]);
+#pragma unroll
+      for (int j = DC - 1; j >= 0; j--) suf[j] = (j == DC - 1) ? x[j] : boxplus(x[j], suf[j + 1]);
+      const float sg = (((sbit + DC) & 1) ? -1.f : 1.f);
+#pragma unroll
+      for (int j = 0; j < DC; j++) {
+        float gg;
+        if (j == 0) gg = suf[1];
+        else if (j == DC - 1) gg = pre[DC - 2];
+        else gg = boxplus(pre[j - 1], suf[j + 1]);
+        gg = sg * gg;
+        out[j] = (gg == 0.f) ? 0.f : gg;
+      }
+    }
+  }
+  T res[DC];
+#pragma unroll
+  for (int j = 0; j < DC; j++) M::st(res + j, update(P, A(0), out[j]));
+  RowIO<T, DC>::store(CVn + (size_t)c * DC, res);
+}
+
+// NB checks per step: all their gathers are issued before any of them is used.
+template <int PREC, int RULE, int DC, int DV, int NB, class SBit>
+__device__ __forceinline__ void fused_loop(int rank, int size, const DevCode &C, const DevParams &P,
+                                           const SBit &sbit, const typename MT<PREC>::T *CVp,
+                                           typename MT<PREC>::T *CVn) {
+  int c = rank;
+  for (; c + (NB - 1) * size < C.m; c += NB * size) {
+    FusedIn<PREC, DC, DV> g[NB];
+#pragma unroll
+    for (int i = 0; i < NB; i++) fused_gather<PREC, DC, DV>(C, c + i * size, CVp, g[i]);
+#pragma unroll
+    for (int i = 0; i < NB; i++)
+      fused_compute<PREC, RULE, DC, DV>(C, P, c + i * size, sbit(c + i * size), g[i], CVn);
+  }
+  for (; c < C.m; c += size) {
+    FusedIn<PREC, DC, DV> g;
+    fused_gather<PREC, DC, DV>(C, c, CVp, g);
+    fused_compute<PREC, RULE, DC, DV>(C, P, c, sbit(c), g, CVn);
+  }
+}
+
+// Degree pairs with a fused sweep: 2D toric (4,2), 3D point (6,2), membrane (4,4),
+// bivariate bicycle (6,3), periodic chain (2,2).
+__device__ __forceinline__ bool fused_ok(const DevCode &C) {
+  if (!C.partner) return false;
+  return (C.dc_u == 4 && (C.dv_u == 2 || C.dv_u == 4)) || (C.dc_u == 6 && (C.dv_u == 2 || C.dv_u == 3)) ||
+         (C.dc_u == 2 && C.dv_u == 2);
+}
+
+// The messages live in shared memory (SMEM = true: the pointers are rebased on the
+// dynamic shared-memory window so the compiler emits shared-memory accesses) or
+// in global memory, where more checks per step keep more gathers in flight.
+template <int PREC, int RULE, bool SMEM, int DC, int DV, class SBit>
+__device__ __noinline__ void fused_run(int rank, int size, const DevCode &C, const DevParams &P,
+                                       SBit sbit, const typename MT<PREC>::T *CVp,
+                                       typename MT<PREC>::T *CVn) {
+  using T = typename MT<PREC>::T;
+  if (SMEM) {
+    extern __shared__ __align__(16) uint8_t lim_dyn_smem[];
+    CVp = reinterpret_cast<const T *>(lim_dyn_smem + (reinterpret_cast<const uint8_t *>(CVp) - lim_dyn_smem));
+    CVn = reinterpret_cast<T *>(lim_dyn_smem + (reinterpret_cast<uint8_t *>(CVn) - lim_dyn_smem));
+  }
+  constexpr int NP = DC * (DV - 1);
+  constexpr int NB = SMEM ? 2 : (NP <= 4 ? 4 : (NP <= 6 ? 2 : 1));
+  fused_loop<PREC, RULE, DC, DV, NB>(rank, size, C, P, sbit, CVp, CVn);
+}
+
+template <int PREC, int RULE, bool SMEM, class SBit>
+__device__ __forceinline__ void fused_pass(int rank, int size, const DevCode &C, const DevParams &P,
+                                           SBit sbit, const typename MT<PREC>::T *CVp,
+                                           typename MT<PREC>::T *CVn) {
+  if (C.dc_u == 4 && C.dv_u == 2) fused_run<PREC, RULE, SMEM, 4, 2>(rank, size, C, P, sbit, CVp, CVn);
+  else if (C.dc_u == 6 && C.dv_u == 2) fused_run<PREC, RULE, SMEM, 6, 2>(rank, size, C, P, sbit, CVp, CVn);
+  else if (C.dc_u == 4 && C.dv_u == 4) fused_run<PREC, RULE, SMEM, 4, 4>(rank, size, C, P, sbit, CVp, CVn);
+  else if (C.dc_u == 6 && C.dv_u == 3) fused_run<PREC, RULE, SMEM, 6, 3>(rank, size, C, P, sbit, CVp, CVn);
+  else fused_run<PREC, RULE, SMEM, 2, 2>(rank, size, C, P, sbit, CVp, CVn);
 }
 
 struct SBitWords {  // s~ from bit-packed words

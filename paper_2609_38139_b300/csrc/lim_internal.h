@@ -29,6 +29,9 @@ struct DevCode {
   int32_t nw, mw;              // words of the bit vectors e and s
   int32_t dc_max, dv_max;
   int32_t var_cls, chk_cls;    // degree classes of the half-sweeps
+  int32_t dv_u, dc_u;          // uniform qubit / check degree, 0 if irregular
+  const int32_t *partner;      // [E*(dv_u-1)]: a qubit's other edges per edge (uniform
+                               // degrees), ascending check order, or null
   const int32_t *c_ptr;        // [m+1]
   const int32_t *c_var;        // [E]
   const int32_t *v_ptr;        // [n+1]
@@ -52,7 +55,7 @@ struct DevPoint {
 // Scalars of the method in the working arithmetic (binary32 or int32 steps).
 struct DevParams {
   int32_t rule, feedback, prec, K, gauge_on_move;
-  int32_t alpha_is_one;
+  int32_t alpha_is_one, profile;
   float pi_f, clamp_f, alpha_f;
   int32_t pi_q, clamp_q, A;
   float theta_f[kMaxDeg + 1];    // evidence threshold by check degree
@@ -95,6 +98,7 @@ CodeLayout code_layout(const DevCode &c, int prec);
 struct HostCode {
   int32_t n = 0, m = 0, E = 0, k = 0;
   std::vector<int32_t> c_ptr, c_var, v_ptr, v_edge, v_chk;
+  std::vector<int32_t> partner;  // see DevCode::partner
   std::vector<uint32_t> logicals;
   int32_t dc_min = 0, dc_max = 0, dv_min = 0, dv_max = 0;
 };
@@ -116,6 +120,10 @@ int launch_batch(const LaunchArgs &args, int variant_warp, int grid, int block, 
                  void *stream);
 int batch_occupancy(int warp, int prec, int rule, int fb, int block, size_t smem,
                     int *blocks_per_sm);
+// Plain baseline: per-shot HBM slot size, and the init / tick / finish kernels.
+size_t plain_slot_bytes(const DevCode &c, int prec);
+int launch_plain(const LaunchArgs &args, int kind, int t, int *running, int grid, int block,
+                 void *stream);  // kind 0 init, 1 tick, 2 finish
 int launch_noise(const DevCode &c, uint64_t p_thr, uint32_t seed_lo, uint32_t seed_hi,
                  uint32_t point_id, uint32_t shot0, uint32_t nshots, uint32_t *e_bits,
                  uint32_t *s_bits, void *stream);

@@ -16,6 +16,7 @@ const void *batch_fn_f16(int warp, int rule, int fb);
 const void *batch_fn_bf16(int warp, int rule, int fb);
 const void *batch_fn_i16(int warp, int rule, int fb);
 const void *batch_fn_i8(int warp, int rule, int fb);
+void plain_fns_f32(int rule, int fb, const void **init, const void **tick, const void **finish);
 
 namespace {
 
@@ -144,6 +145,27 @@ int launch_batch(const LaunchArgs &args, int warp, int grid, int block, size_t s
   err = cudaLaunchKernel(fn, dim3(grid), dim3(block), params, smem, (cudaStream_t)stream);
   if (err != cudaSuccess) return cuda_fail(err, "batch kernel launch");
   return LIM_OK;
+}
+
+size_t plain_slot_bytes(const DevCode &c, int prec) {
+  const CodeLayout l = code_layout(c, prec);
+  return (l.bits_bytes + l.msg_bytes + l.chk_bytes + 255) & ~size_t(255);
+}
+
+int launch_plain(const LaunchArgs &args, int kind, int t, int *running, int grid, int block,
+                 void *stream) {
+  if (args.prm.prec != LIM_PREC_F32) {
+    set_error("the plain baseline path supports binary32 messages only");
+    return LIM_E_UNSUPPORTED;
+  }
+  const void *fi, *ft, *ff;
+  plain_fns_f32(args.prm.rule, args.prm.feedback, &fi, &ft, &ff);
+  const void *fn = kind == 0 ? fi : (kind == 1 ? ft : ff);
+  void *p_args[] = {const_cast<LaunchArgs *>(&args)};
+  void *p_tick[] = {const_cast<LaunchArgs *>(&args), &t, &running};
+  cudaError_t err = cudaLaunchKernel(fn, dim3(grid), dim3(block), kind == 1 ? p_tick : p_args, 0,
+                                     (cudaStream_t)stream);
+  return err == cudaSuccess ? LIM_OK : cuda_fail(err, "plain kernel launch");
 }
 
 int launch_noise(const DevCode &c, uint64_t p_thr, uint32_t seed_lo, uint32_t seed_hi,

@@ -26,6 +26,8 @@ VARIANT = {"auto": 0, "cta": 1, "warp": 2, "plain": 3}
 SECTOR = {"point": 0, "membrane": 1}
 MSG_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "i16": 2, "i8": 1}
 HIST_BINS = 24
+PHASES = ["init", "feedback_scan_and_qubit_half_sweep", "move_resolution", "check_half_sweep",
+          "further_sweeps", "finish"]
 MAX_POINTS = 128
 
 # Every extern "C" symbol declared in include/lim.h.
@@ -53,7 +55,8 @@ class Params(ctypes.Structure):
                 ("dt_tick", ctypes.c_double), ("sweeps_per_tick", ctypes.c_int32),
                 ("ring_prob", ctypes.c_double), ("tick_budget", ctypes.c_int32),
                 ("gauge_on_move", ctypes.c_int32), ("variant", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("profile", ctypes.c_int32)]
 
 
 class Point(ctypes.Structure):
@@ -66,7 +69,8 @@ RECORD_DTYPE = np.dtype([("t_clr", np.int32), ("converged", np.int32), ("failed"
                          ("moves", np.int32), ("ticks", np.int64), ("sweeps", np.int64)])
 TALLY_FIELDS = ["shots", "failures", "nonconverged", "sum_t", "sum_t2", "moves", "ticks", "sweeps",
                 "msg_updates", "errors"]
-TALLY_DTYPE = np.dtype([(f, np.int64) for f in TALLY_FIELDS] + [("hist", np.int64, (HIST_BINS,))])
+TALLY_DTYPE = np.dtype([(f, np.int64) for f in TALLY_FIELDS] + [("hist", np.int64, (HIST_BINS,)),
+                                                                ("phase_cycles", np.int64, (len(PHASES),))])
 
 _lib: Optional[ctypes.CDLL] = None
 
@@ -117,11 +121,11 @@ def check(st: int, what: str = "") -> None:
 
 def params(rule="minsum", feedback="check_move", precision="f32", quant_scale=2.0 ** -6, q=0.05,
            clamp=1000.0, tau=0.1, dt_tick=0.1, sweeps_per_tick=1, ring_prob=-1.0, tick_budget=32,
-           gauge_on_move=0, variant="auto", block_threads=0, blocks_per_sm=0) -> Params:
+           gauge_on_move=0, variant="auto", block_threads=0, blocks_per_sm=0, profile=0) -> Params:
     return Params(RULE[rule], FEEDBACK[feedback], PREC[precision], float(quant_scale), float(q),
                   float(clamp), float(tau), float(dt_tick), int(sweeps_per_tick), float(ring_prob),
                   int(tick_budget), int(gauge_on_move), VARIANT[variant], int(block_threads),
-                  int(blocks_per_sm))
+                  int(blocks_per_sm), int(profile))
 
 
 def prec_name(prm: Params) -> str:

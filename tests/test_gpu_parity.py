@@ -309,3 +309,20 @@ def test_full_size_toric2d_sampled(L, ctx, L_, p, shots):
     code = I.toric2d(L_)
     prm = L.params(precision="f32", tick_budget=40 * L_, variant="cta")
     _batch_vs_oracle(L, ctx, code, prm, p, shots, seed=0, point_id=5, shot0=1000, finals=False)
+
+
+@pytest.mark.parametrize("rule,fb", [("minsum", "check_move"), ("minsum", "bit_discrete"),
+                                     ("sumproduct", "check_move")])
+def test_plain_path_equals_batched_kernel(L, ctx, rule, fb):
+    """The plain baseline (one launch per tick, host-polled termination, HBM
+    state) computes the same trajectories as the persistent kernel."""
+    c6, c8 = ctx.from_inputs(I.toric2d(6)), ctx.from_inputs(I.toric2d(8))
+    pts = [(c6, 0.05, 50, 0, 0, 60), (c8, 0.07, 30, 5, 1, 40)]
+    kw = dict(precision="f32", rule=rule, feedback=fb, tick_budget=60)
+    tal_b, rec_b = L.run_batch(ctx, pts, L.params(**kw), 9)
+    tal_p, rec_p = L.run_batch(ctx, pts, L.params(variant="plain", **kw), 9)
+    assert np.array_equal(rec_p, rec_b)
+    assert np.array_equal(tal_p, tal_b)
+    if rule == "minsum":
+        ora = oracle_point(I.toric2d(6), L.params(**kw), 0.05, 9, 0, 0, 50)
+        compare_records(rec_p[:50], ora, "plain")
