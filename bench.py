@@ -104,6 +104,32 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def kernel_source_hash() -> str:
+    """Hash of the CUDA sources: a traffic figure measured on other sources is stale."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2609_38139_b300", "csrc")
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+                    glob.glob(os.path.join(csrc, "*.h"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str, prec: str, algorithmic_bytes_per_launch: float):
+    """DRAM bytes per launch from the committed ncu summary of this workload, scaled
+    to this run's launches by their algorithmic bytes; None if the summary was
+    taken on other kernel sources or another workload."""
+    f = os.path.join(ROOT, "profiles", f"batch_kernel__{workload}__{prec}__dram.json")
+    try:
+        d = json.load(open(f))
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d["dram_bytes"] * algorithmic_bytes_per_launch / d["algorithmic_bytes"]
+
+
 def peak_hbm():
     try:
         d = json.load(open(PEAKS_FILE))
@@ -200,9 +226,14 @@ def main():
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--phases", action="store_true", help="report the kernel's per-phase cycle shares")
+    ap.add_argument("--autotune", action="store_true", help="pick the launch shape with lim_autotune")
+    ap.add_argument("--print-source-hash", action="store_true")
     ap.add_argument("--sizes", default="", help="comma list restricting the code sizes")
     ap.add_argument("--ps", default="", help="comma list restricting the error rates")
     args = ap.parse_args()
+    if args.print_source_hash:
+        print(kernel_source_hash())
+        return 0
     if args.impl == "reference":
         return run_reference(args)
 
@@ -236,6 +267,13 @@ def main():
         return [(codes[(d["family"], d["size"])], d["p"], d["shots"], base, d["point_id"], d["T"])
                 for d in pts]
 
+    tuned = None
+    if args.autotune:
+        best, rate = L.autotune(ctx, step_points(0), prm, sample_shots=8, sample_ticks=128)
+        best.profile = prm.profile
+        prm = best
+        tuned = {"variant": int(prm.variant), "block_threads": int(prm.block_threads),
+                 "blocks_per_sm": int(prm.blocks_per_sm), "sample_rate": rate}
     batch = L.Batch(ctx, step_points(0), prm, records=True)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 126 MB L2
@@ -297,17 +335,23 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": args.workload, "codes": "toric2d L=16,32,64,128",
+            "config": {"workload": args.workload, "codes": f"{w['family']} sizes {w['sizes']}",
                        "points": len(pts), "shots_per_point_per_step": args.shots,
                        "shots_per_step": shots // max(1, args.steps) // world,
-                       "rule": "minsum", "feedback": "check_move", "sweeps_per_tick": w["K"],
-                       "tick_budget": "40L", "variant": args.variant,
+                       "rule": "minsum",
+                       "feedback": "bit_discrete" if args.workload == "rep2000_p045" else "check_move",
+                       "sweeps_per_tick": w.get("K", 1), "tick_budget": w["budget"],
+                       "variant": args.variant,
                        "l2": "flushed between steps (256 MiB write, outside the timed window)",
-                       "parallelism": f"replicas x{world}, disjoint shot ids"},
+                       "parallelism": f"replicas x{world}, disjoint shot ids",
+                       "launch_shape": tuned or "library default"},
             "msg_updates_per_s": upd_rate,
             "ler_sample": fails / max(1, shots),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
+                         "frac": achieved / hbm,
+                         "traffic": measured_traffic(args.workload, args.precision,
+                                                     upd * 2 * bpm / args.steps / world),
+                         "algorithmic_bytes_per_launch": upd * 2 * bpm / args.steps / world,
                          "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)",
                          "kernel": "batch_kernel (persistent)",
                          "algorithmic_bytes": "2 x msg bytes per message update (read old, write new)"},
@@ -317,16 +361,19 @@ def main():
         line["phase_cycles_per_tick"] = float(phase.sum() / max(1, ticks))
     # end to end through the public API: run + read records and tallies back
     if not args.no_e2e:
+        # the batch captured once as a CUDA graph (lim_graph_create) and replayed
+        # with a fresh shot window per step; records and tallies read back
         rec_host = torch.empty(batch.rec.numel(), dtype=torch.uint8, pin_memory=True)
         tal_host = torch.empty(batch.tally.numel(), dtype=torch.uint8, pin_memory=True)
+        batch.points = step_points(0)
+        batch.pts = L._points(batch.points)
+        batch.capture()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e_ticks = 0
         for i in range(args.steps):
-            batch.points = step_points(step_id[0])
-            batch.pts = L._points(batch.points)
+            batch.replay(0, (step_id[0] * world) * args.shots, stream)
             step_id[0] += 1
-            batch.run(0, stream)
             rec_host.copy_(batch.rec, non_blocking=True)
             tal_host.copy_(batch.tally, non_blocking=True)
             torch.cuda.synchronize()
@@ -336,8 +383,8 @@ def main():
         line["e2e"] = {"value": e_ticks / e_dt * world, "unit": "shot-ticks/s",
                        "h2d_bytes_per_step": 0,
                        "d2h_bytes_per_step": int(batch.rec.numel() + batch.tally.numel()),
-                       "note": "noise is sampled on the device (part of the method); the point "
-                               "list travels as launch parameters; records and tallies are read back"}
+                       "note": "graph replay per step (lim_graph_launch); noise is sampled on the "
+                               "device (part of the method); records and tallies are read back"}
         line["gpu_launches"] = args.steps
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.precision, args.cpu_seconds)

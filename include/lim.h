@@ -238,6 +238,29 @@ int lim_run_batch_static(lim_ctx *ctx, const lim_point *pts, uint32_t npts, cons
                          uint64_t seed, lim_shot_record *rec, uint32_t *e_final, lim_tally *tally,
                          void *stream);
 
+/* A batch captured once as a CUDA graph (work-queue reset, tally reset, the
+ * persistent kernel) and replayed with a new seed and shot window each launch:
+ * launch i runs shots shot0 + shot_offset ... of every point.  The buffers given
+ * at creation (workspace, rec, e_final, tally) are used by every launch and
+ * must outlive the graph; launches on one stream serialise.  Same results as
+ * lim_run_batch with the same seed and shot ids.  Variant PLAIN is refused. */
+typedef struct lim_graph lim_graph;
+int lim_graph_create(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+                     void *workspace, size_t workspace_bytes, lim_shot_record *rec,
+                     uint32_t *e_final, lim_tally *tally, lim_graph **out);
+int lim_graph_launch(lim_graph *graph, uint64_t seed, uint32_t shot_offset, void *stream);
+int lim_graph_destroy(lim_graph *graph);
+
+/* Autotuner: times the persistent kernel's launch shapes (one block or one warp
+ * per shot, block sizes, blocks per SM) on a sample of the batch -- every point
+ * with at most sample_shots shots and at most sample_ticks ticks -- and writes
+ * the fastest into best->variant / block_threads / blocks_per_sm (the other
+ * fields are copied from prm).  Results never depend on the shape (randomness
+ * is keyed by shot), only speed does.  Allocates and frees its own scratch,
+ * synchronises the device; rate_out (nullable) gets the best shot-ticks/s. */
+int lim_autotune(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+                 uint32_t sample_shots, int32_t sample_ticks, lim_params *best, double *rate_out);
+
 /* Words per shot of lim_run_batch's e_final rows for this point list. */
 int lim_final_words(const lim_point *pts, uint32_t npts, int32_t *words);
 

@@ -598,6 +598,196 @@ int lim_run_batch(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_p
   });
 }
 
+}  // extern "C"
+
+struct lim_graph {
+  lim_ctx *ctx;
+  lim::LaunchArgs args;
+  std::vector<uint32_t> shot0;  // per point, as given at creation
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t kernel = nullptr;
+  cudaKernelNodeParams kp{};
+  void *kargs[1];
+};
+
+extern "C" {
+
+int lim_graph_create(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+                     void *workspace, size_t workspace_bytes, lim_shot_record *rec,
+                     uint32_t *e_final, lim_tally *tally, lim_graph **out) {
+  return guarded([&] {
+    if (!out || !tally || !workspace) return bad(LIM_E_INVAL, "null argument");
+    DevParams dp;
+    int st = derive(prm, dp);
+    if (st) return st;
+    Plan pl;
+    st = make_plan(ctx, pts, npts, prm, dp, pl);
+    if (st) return st;
+    if (pl.plain) return bad(LIM_E_UNSUPPORTED, "the plain path is not graph-captured");
+    if (workspace_bytes < pl.workspace) return bad(LIM_E_NOMEM, "workspace too small");
+    lim_graph *g = new (std::nothrow) lim_graph();
+    if (!g) return bad(LIM_E_NOMEM, "host allocation failed");
+    g->ctx = ctx;
+    fill_args(pl, pts, npts, prm, dp, 0, workspace, g->args);
+    g->args.rec = rec;
+    g->args.e_final = e_final;
+    if (e_final) lim_final_words(pts, npts, &g->args.e_final_words);
+    g->args.tally = tally;
+    for (uint32_t i = 0; i < npts; i++) g->shot0.push_back(pts[i].shot0);
+    cudaError_t err = cudaGraphCreate(&g->graph, 0);
+    cudaGraphNode_t m1 = nullptr, m2 = nullptr;
+    if (err == cudaSuccess) {
+      cudaMemsetParams mp{};
+      mp.dst = workspace;
+      mp.value = 0;
+      mp.elementSize = 1;
+      mp.width = 256;
+      mp.height = 1;
+      err = cudaGraphAddMemsetNode(&m1, g->graph, nullptr, 0, &mp);
+      if (err == cudaSuccess) {
+        mp.dst = tally;
+        mp.width = sizeof(lim_tally) * npts;
+        err = cudaGraphAddMemsetNode(&m2, g->graph, nullptr, 0, &mp);
+      }
+    }
+    const void *fn = nullptr;
+    if (err == cudaSuccess) {
+      int occ = 0;
+      st = batch_occupancy(pl.warp, dp.prec, dp.rule, dp.feedback, pl.block, pl.smem, &occ);
+      if (st) {
+        lim_graph_destroy(g);
+        return st;
+      }
+      fn = batch_fn_ptr(pl.warp, dp.prec, dp.rule, dp.feedback);
+      g->kargs[0] = &g->args;
+      g->kp.func = const_cast<void *>(fn);
+      g->kp.gridDim = dim3(pl.grid);
+      g->kp.blockDim = dim3(pl.block);
+      g->kp.sharedMemBytes = (unsigned)pl.smem;
+      g->kp.kernelParams = g->kargs;
+      g->kp.extra = nullptr;
+      cudaGraphNode_t deps[2] = {m1, m2};
+      err = cudaGraphAddKernelNode(&g->kernel, g->graph, deps, 2, &g->kp);
+    }
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (err != cudaSuccess) {
+      lim_graph_destroy(g);
+      return cuda_fail(err, "graph construction");
+    }
+    *out = g;
+    return LIM_OK;
+  });
+}
+
+int lim_graph_launch(lim_graph *g, uint64_t seed, uint32_t shot_offset, void *stream) {
+  return guarded([&] {
+    if (!g) return bad(LIM_E_INVAL, "null graph");
+    g->args.prm.seed_lo = (uint32_t)seed;
+    g->args.prm.seed_hi = (uint32_t)(seed >> 32);
+    for (int i = 0; i < g->args.npts; i++) {
+      if ((uint64_t)g->shot0[i] + shot_offset + g->args.pts[i].shots > (1ull << 32))
+        return bad(LIM_E_INVAL, "shot ids exceed 2^32");
+      g->args.pts[i].shot0 = g->shot0[i] + shot_offset;
+    }
+    cudaError_t err = cudaGraphExecKernelNodeSetParams(g->exec, g->kernel, &g->kp);
+    if (err == cudaSuccess) err = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+    return err == cudaSuccess ? LIM_OK : cuda_fail(err, "graph launch");
+  });
+}
+
+int lim_graph_destroy(lim_graph *g) {
+  if (!g) return LIM_OK;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+  return LIM_OK;
+}
+
+int lim_autotune(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+                 uint32_t sample_shots, int32_t sample_ticks, lim_params *best, double *rate_out) {
+  return guarded([&] {
+    if (!ctx || !pts || !prm || !best || npts == 0) return bad(LIM_E_INVAL, "null argument");
+    if (ctx->device < 0) return bad(LIM_E_INVAL, "host-only context cannot run kernels");
+    std::vector<lim_point> sample(pts, pts + npts);
+    for (auto &p : sample) {
+      p.shots = std::min(p.shots, std::max(1u, sample_shots));
+      int32_t T = p.tick_budget > 0 ? p.tick_budget : prm->tick_budget;
+      if (sample_ticks > 0) p.tick_budget = std::min(T, sample_ticks);
+    }
+    struct Shape {
+      int variant, block, bpsm;
+    };
+    const Shape shapes[] = {{LIM_VARIANT_CTA, 1024, 1}, {LIM_VARIANT_CTA, 512, 2},
+                            {LIM_VARIANT_CTA, 512, 1},  {LIM_VARIANT_CTA, 256, 4},
+                            {LIM_VARIANT_WARP, 256, 0}, {LIM_VARIANT_WARP, 512, 0},
+                            {LIM_VARIANT_WARP, 128, 0}};
+    double best_rate = -1;
+    lim_params best_p = *prm;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    lim_tally *tally = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaMalloc((void **)&tally, sizeof(lim_tally) * npts);
+    if (err == cudaSuccess) err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    int st = err == cudaSuccess ? LIM_OK : cuda_fail(err, "autotune setup");
+    for (const Shape &sh : shapes) {
+      if (st) break;
+      lim_params p = *prm;
+      p.variant = sh.variant;
+      p.block_threads = sh.block;
+      p.blocks_per_sm = sh.bpsm;
+      size_t need = 0;
+      if (lim_workspace_size(ctx, sample.data(), npts, &p, &need) != LIM_OK) continue;  // shape does not fit
+      if (need > ws_bytes) {
+        if (ws) cudaFree(ws);
+        ws = nullptr;
+        err = cudaMalloc(&ws, need);
+        if (err != cudaSuccess) {
+          st = cuda_fail(err, "autotune workspace");
+          break;
+        }
+        ws_bytes = need;
+      }
+      float ms = 0;
+      for (int rep = 0; rep < 2 && !st; rep++) {  // first run warms up
+        cudaEventRecord(e0, 0);
+        st = lim_run_batch(ctx, sample.data(), npts, &p, 1, ws, ws_bytes, nullptr, nullptr, tally, 0);
+        cudaEventRecord(e1, 0);
+        if (!st) {
+          err = cudaEventSynchronize(e1);
+          if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+          if (err != cudaSuccess) st = cuda_fail(err, "autotune timing");
+        }
+      }
+      if (st) break;
+      std::vector<lim_tally> host(npts);
+      err = cudaMemcpy(host.data(), tally, sizeof(lim_tally) * npts, cudaMemcpyDeviceToHost);
+      if (err != cudaSuccess) {
+        st = cuda_fail(err, "autotune tally");
+        break;
+      }
+      double ticks = 0;
+      for (auto &t : host) ticks += (double)t.ticks;
+      const double rate = ms > 0 ? ticks / (ms * 1e-3) : 0;
+      if (rate > best_rate) {
+        best_rate = rate;
+        best_p = p;
+      }
+    }
+    if (ws) cudaFree(ws);
+    if (tally) cudaFree(tally);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) return st;
+    if (best_rate < 0) return bad(LIM_E_UNSUPPORTED, "no launch shape fits these codes");
+    *best = best_p;
+    if (rate_out) *rate_out = best_rate;
+    return LIM_OK;
+  });
+}
+
 int lim_trace(lim_ctx *ctx, const lim_code *code, const lim_params *prm, double p, uint64_t seed,
               uint32_t point_id, uint32_t shot, int32_t max_ticks, void *workspace,
               size_t workspace_bytes, uint32_t *e_hist, uint32_t *s_hist, lim_shot_record *rec,

@@ -118,6 +118,7 @@ void set_error(const std::string &msg);
 // Kernel launchers (lim_kernels.cu).
 int launch_batch(const LaunchArgs &args, int variant_warp, int grid, int block, size_t smem,
                  void *stream);
+const void *batch_fn_ptr(int warp, int prec, int rule, int fb);
 int batch_occupancy(int warp, int prec, int rule, int fb, int block, size_t smem,
                     int *blocks_per_sm);
 // Plain baseline: per-shot HBM slot size, and the init / tick / finish kernels.

@@ -123,6 +123,8 @@ CodeLayout code_layout(const DevCode &c, int prec) {
   return L;
 }
 
+const void *batch_fn_ptr(int warp, int prec, int rule, int fb) { return batch_fn(warp, prec, rule, fb); }
+
 int batch_occupancy(int warp, int prec, int rule, int fb, int block, size_t smem,
                     int *blocks_per_sm) {
   const void *fn = batch_fn(warp, prec, rule, fb);

@@ -34,7 +34,8 @@ MAX_POINTS = 128
 EXPORTS = ["lim_last_error", "lim_version", "lim_ctx_create", "lim_ctx_destroy", "lim_code_from_csr",
            "lim_code_rep", "lim_code_toric2d", "lim_code_toric3d", "lim_code_bb", "lim_code_info",
            "lim_code_export", "lim_code_destroy", "lim_sample_noise", "lim_params_check",
-           "lim_workspace_size", "lim_run_batch", "lim_run_batch_static", "lim_final_words",
+           "lim_workspace_size", "lim_run_batch", "lim_run_batch_static", "lim_graph_create",
+           "lim_graph_launch", "lim_graph_destroy", "lim_autotune", "lim_final_words",
            "lim_trace", "lim_bp_sweeps", "lim_readout"]
 
 
@@ -103,6 +104,12 @@ def lib() -> ctypes.CDLL:
     L.lim_run_batch.argtypes = [vp, vp, u32, ctypes.POINTER(Params), u64, vp, ctypes.c_size_t, vp, vp,
                                 vp, vp]
     L.lim_run_batch_static.argtypes = [vp, vp, u32, ctypes.POINTER(Params), u64, vp, vp, vp, vp]
+    L.lim_graph_create.argtypes = [vp, vp, u32, ctypes.POINTER(Params), vp, ctypes.c_size_t, vp, vp,
+                                   vp, pp]
+    L.lim_graph_launch.argtypes = [vp, u64, u32, vp]
+    L.lim_graph_destroy.argtypes = [vp]
+    L.lim_autotune.argtypes = [vp, vp, u32, ctypes.POINTER(Params), u32, i32, ctypes.POINTER(Params),
+                               ctypes.POINTER(ctypes.c_double)]
     L.lim_final_words.argtypes = [vp, u32, ctypes.POINTER(i32)]
     L.lim_trace.argtypes = [vp, vp, ctypes.POINTER(Params), dbl, u64, u32, u32, i32, vp,
                             ctypes.c_size_t, vp, vp, vp, vp]
@@ -289,6 +296,28 @@ class Batch:
                                   None if self.e_final is None else self.e_final.data_ptr(),
                                   self.tally.data_ptr(), st), "lim_run_batch")
 
+    def capture(self) -> None:
+        """Capture this batch as a CUDA graph (lim_graph_create) for replay()."""
+        h = ctypes.c_void_p()
+        check(lib().lim_graph_create(self.ctx.handle, self.pts, len(self.points), ctypes.byref(self.prm),
+                                     self.ws.data_ptr(), self.ws_bytes,
+                                     None if self.rec is None else self.rec.data_ptr(),
+                                     None if self.e_final is None else self.e_final.data_ptr(),
+                                     self.tally.data_ptr(), ctypes.byref(h)), "lim_graph_create")
+        self.graph = h
+
+    def replay(self, seed: int, shot_offset: int, stream=None) -> None:
+        check(lib().lim_graph_launch(self.graph, int(seed), int(shot_offset), _stream_ptr(stream)),
+              "lim_graph_launch")
+
+    def __del__(self):
+        g = getattr(self, "graph", None)
+        if g:
+            try:
+                lib().lim_graph_destroy(g)
+            except Exception:
+                pass
+
     def tallies(self) -> np.ndarray:
         return np.frombuffer(self.tally.cpu().numpy().tobytes(), dtype=TALLY_DTYPE).copy()
 
@@ -309,6 +338,16 @@ def run_batch(ctx: Context, points, prm: Params, seed: int, e_final: bool = Fals
     torch.cuda.synchronize(ctx.device)
     out = (b.tallies(), b.records())
     return out + ((b.finals(),) if e_final else ())
+
+
+def autotune(ctx: Context, points, prm: Params, sample_shots: int = 4, sample_ticks: int = 64):
+    """(best Params, shot-ticks/s of the best shape on the sample) from lim_autotune."""
+    pts = _points(points)
+    best = Params()
+    rate = ctypes.c_double()
+    check(lib().lim_autotune(ctx.handle, pts, len(points), ctypes.byref(prm), int(sample_shots),
+                             int(sample_ticks), ctypes.byref(best), ctypes.byref(rate)), "lim_autotune")
+    return best, rate.value
 
 
 def run_batch_static(ctx: Context, points, prm: Params, seed: int, stream=None):

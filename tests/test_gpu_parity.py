@@ -326,3 +326,33 @@ def test_plain_path_equals_batched_kernel(L, ctx, rule, fb):
     if rule == "minsum":
         ora = oracle_point(I.toric2d(6), L.params(**kw), 0.05, 9, 0, 0, 50)
         compare_records(rec_p[:50], ora, "plain")
+
+
+def test_graph_replay_equals_run_batch(L, ctx):
+    """A batch captured as a CUDA graph and replayed with new seeds and shot
+    windows gives exactly the results of direct lim_run_batch calls."""
+    c8 = ctx.from_inputs(I.toric2d(8))
+    bb = ctx.from_inputs(I.bb_code(6, 6))
+    prm = L.params(precision="f32", tick_budget=40)
+    pts = [(c8, 0.05, 64, 10, 0), (bb, 0.04, 64, 10, 1)]
+    b = L.Batch(ctx, pts, prm)
+    b.capture()
+    for seed, off in ((3, 0), (4, 500)):
+        b.replay(seed, off)
+        torch.cuda.synchronize()
+        shifted = [(c, p, n, s0 + off, pid) for c, p, n, s0, pid in pts]
+        tal, rec = L.run_batch(ctx, shifted, prm, seed)
+        assert np.array_equal(b.records(), rec)
+        assert np.array_equal(b.tallies(), tal)
+
+
+def test_autotuner_picks_a_working_shape(L, ctx):
+    c16 = ctx.from_inputs(I.toric2d(16))
+    bb = ctx.from_inputs(I.bb_code(12, 6))
+    prm = L.params(precision="f32", tick_budget=64)
+    pts = [(c16, 0.06, 32, 0, 0), (bb, 0.04, 32, 0, 1)]
+    best, rate = L.autotune(ctx, pts, prm, sample_shots=8, sample_ticks=32)
+    assert rate > 0 and best.variant in (1, 2)
+    _, rec_a = L.run_batch(ctx, pts, prm, 5)
+    _, rec_b = L.run_batch(ctx, pts, best, 5)
+    assert np.array_equal(rec_a, rec_b)  # the shape never changes results
