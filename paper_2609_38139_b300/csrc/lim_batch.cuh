@@ -24,7 +24,8 @@ struct TeamCtl {
   int32_t err;
   uint32_t logmask; // parities of e with the X-logicals
   int32_t t_clr, converged, ticks, sweeps, vc_sel, done;
-  int32_t pad[3];
+  int32_t work;     // chunk counter of the dynamically distributed sweep
+  int32_t pad[2];
 };
 static_assert(sizeof(TeamCtl) == 64, "TeamCtl layout");
 
@@ -218,6 +219,8 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
   const bool frame_s0 = (FB == LIM_FB_BIT_DISCRETE) || P.gauge_on_move;
   const uint32_t *seff = frame_s0 ? V.s0 : V.s;  // effective syndrome of the check half-sweep
   R.ticks = t;
+  // the sweep's chunk counter; published by the barrier after the feedback scan
+  if (!Team::is_warp && tm.rank() == 0) ctl->work = 0;
   // --- read-out + feedback (+ the qubit half-sweep of sweep 1, which reads the
   //     same messages and does not depend on the feedback) --------------------
   if (FB == LIM_FB_CHECK_MOVE) {
@@ -380,16 +383,21 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
   if (t == pt.T) return true;
   // --- check half-sweep of sweep 1, then sweeps 2..K ---------------------------
   if (fused) {
+    int32_t *work = Team::is_warp ? nullptr : &ctl->work;
     for (int k = 0; k < P.K; k++) {
+      if (k > 0 && work) {  // reset the chunk counter between sweeps
+        if (tm.rank() == 0) ctl->work = 0;
+        tm.sync();
+      }
       // The very first sweep maps m = 0 to CV = 0 (every check has degree >= 2),
       // which the zeroed second buffer already holds.
       if (R.sweeps > 0) {
         if (pt.msg_smem)
           fused_pass<PREC, RULE, true>(tm.rank(), tm.size(), C, P, SBitWords{seff},
-                                       B[(R.vc_sel + 2) % 3], B[(R.vc_sel + 1) % 3]);
+                                       B[(R.vc_sel + 2) % 3], B[(R.vc_sel + 1) % 3], work);
         else
           fused_pass<PREC, RULE, false>(tm.rank(), tm.size(), C, P, SBitWords{seff},
-                                        B[(R.vc_sel + 2) % 3], B[(R.vc_sel + 1) % 3]);
+                                        B[(R.vc_sel + 2) % 3], B[(R.vc_sel + 1) % 3], work);
       }
       tm.sync();
       clk.mark(k == 0 ? 3 : 4);

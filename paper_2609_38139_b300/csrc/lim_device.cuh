@@ -219,6 +219,30 @@ __device__ __forceinline__ void flip_bits(const DevCode &C, const FlipCtx &F, in
   atomicAdd(F.moves, 1);
 }
 
+// Min-sum form of Eq. 2 for one check of N inputs: out_j = (-1)^{s_c+d_c} prod_{w!=j}
+// sgn(x_w) min_{w!=j} |x_w|, sgn(0) = +1, a zero magnitude stored as +0.  The two
+// smallest magnitudes are tracked branch-free (ties keep min2 = min1), and the
+// minimum over the others is min2 exactly where |x_j| equals min1.
+template <class A, int N>
+__device__ __forceinline__ void minsum_row(const A (&x)[N], int neg, A (&out)[N]) {
+  A a[N];
+  A min1 = inf_of(A(0)), min2 = inf_of(A(0));
+#pragma unroll
+  for (int j = 0; j < N; j++) {
+    a[j] = absw(x[j]);
+    neg ^= (x[j] < A(0));
+    const A t = max(min1, a[j]);
+    min1 = min(min1, a[j]);
+    min2 = min(min2, t);
+  }
+#pragma unroll
+  for (int j = 0; j < N; j++) {
+    const A mag = (a[j] == min1) ? min2 : min1;
+    const bool ng = neg ^ (x[j] < A(0));
+    out[j] = (mag == A(0)) ? A(0) : (ng ? -mag : mag);
+  }
+}
+
 // Eq. 1 for every edge of qubit v: VCn[e] = update(VCc[e], pi + sum_{c' != c} CV[c'->v]),
 // summed in ascending check order (the order of N(v)).  With READOUT also
 // Eq. 3, L_v = pi + sum_c CV[c->v], and the bit-centric feedback f_v = 1[L_v > 0]
@@ -339,28 +363,32 @@ __device__ __forceinline__ void check_one(const DevCode &C, const DevParams &P, 
   }
   A out[DC];
   if (RULE == LIM_RULE_MINSUM || M::is_int) {
-    int neg = (sbit + d) & 1;  // (-1)^{s_c + d_c}
-    A min1 = inf_of(A(0)), min2 = inf_of(A(0));
-    int imin = -1;
+    if (EXACT) {
+      minsum_row<A, DC>(x, (sbit + d) & 1, out);
+    } else {
+      int neg = (sbit + d) & 1;  // (-1)^{s_c + d_c}
+      A min1 = inf_of(A(0)), min2 = inf_of(A(0));
+      int imin = -1;
 #pragma unroll
-    for (int j = 0; j < DC; j++) {
-      if (EXACT || j < d) {
-        const A a = absw(x[j]);
-        neg ^= (x[j] < A(0));
-        if (a < min1) {
-          min2 = min1;
-          min1 = a;
-          imin = j;
-        } else if (a < min2) {
-          min2 = a;
+      for (int j = 0; j < DC; j++) {
+        if (j < d) {
+          const A a = absw(x[j]);
+          neg ^= (x[j] < A(0));
+          if (a < min1) {
+            min2 = min1;
+            min1 = a;
+            imin = j;
+          } else if (a < min2) {
+            min2 = a;
+          }
         }
       }
-    }
 #pragma unroll
-    for (int j = 0; j < DC; j++) {
-      const A mag = (j == imin) ? min2 : min1;
-      const bool ng = neg ^ (x[j] < A(0));
-      out[j] = (mag == A(0)) ? A(0) : (ng ? -mag : mag);
+      for (int j = 0; j < DC; j++) {
+        const A mag = (j == imin) ? min2 : min1;
+        const bool ng = neg ^ (x[j] < A(0));
+        out[j] = (mag == A(0)) ? A(0) : (ng ? -mag : mag);
+      }
     }
   } else {
     if constexpr (!M::is_int) {
@@ -488,28 +516,9 @@ __device__ __forceinline__ void fused_compute(const DevCode &C, const DevParams 
     x[j] = round_to_storage<PREC>(update(P, A(0), acc));
   }
   A out[DC];
-  if (RULE == LIM_RULE_MINSUM || M::is_int) {
-    int neg = (sbit + DC) & 1;
-    A min1 = inf_of(A(0)), min2 = inf_of(A(0));
-    int imin = -1;
-#pragma unroll
-    for (int j = 0; j < DC; j++) {
-      const A a = absw(x[j]);
-      neg ^= (x[j] < A(0));
-      if (a < min1) {
-        min2 = min1;
-        min1 = a;
-        imin = j;
-      } else if (a < min2) {
-        min2 = a;
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < DC; j++) {
-      const A mag = (j == imin) ? min2 : min1;
-      const bool ng = neg ^ (x[j] < A(0));
-      out[j] = (mag == A(0)) ? A(0) : (ng ? -mag : mag);
-    }
+  constexpr bool kMin = RULE == LIM_RULE_MINSUM || M::is_int;
+  if (kMin) {
+    minsum_row<A, DC>(x, (sbit + DC) & 1, out);
   } else {
     if constexpr (!M::is_int) {
       float pre[DC], suf[DC];
@@ -530,8 +539,10 @@ __device__ __forceinline__ void fused_compute(const DevCode &C, const DevParams 
     }
   }
   T res[DC];
+  // alpha = 1 here: the new message is the clamped BP value; a min-sum output is
+  // one of the (already clamped) inputs up to sign, so its clamp is the identity
 #pragma unroll
-  for (int j = 0; j < DC; j++) M::st(res + j, update(P, A(0), out[j]));
+  for (int j = 0; j < DC; j++) M::st(res + j, kMin ? out[j] : update(P, A(0), out[j]));
   RowIO<T, DC>::store(CVn + (size_t)c * DC, res);
 }
 
@@ -556,6 +567,40 @@ __device__ __forceinline__ void fused_loop(int rank, int size, const DevCode &C,
   }
 }
 
+// The same with dynamic work distribution for a block team: warps take chunks of
+// 32*NB checks from a shared counter (reset to 0 before the pass), so warps that
+// finish early take more work instead of waiting at the barrier.
+template <int PREC, int RULE, int DC, int DV, int NB, class SBit>
+__device__ __forceinline__ void fused_loop_dyn(int32_t *work, const DevCode &C, const DevParams &P,
+                                               const SBit &sbit, const typename MT<PREC>::T *CVp,
+                                               typename MT<PREC>::T *CVn) {
+  const int lane = threadIdx.x & 31;
+  constexpr int CH = 32 * NB;
+  for (;;) {
+    int chunk = 0;
+    if (lane == 0) chunk = atomicAdd(work, 1);
+    chunk = __shfl_sync(0xffffffffu, chunk, 0);
+    const int c0 = chunk * CH;
+    if (c0 >= C.m) break;
+    if (c0 + CH <= C.m) {
+      FusedIn<PREC, DC, DV> g[NB];
+#pragma unroll
+      for (int i = 0; i < NB; i++) fused_gather<PREC, DC, DV>(C, c0 + lane + 32 * i, CVp, g[i]);
+#pragma unroll
+      for (int i = 0; i < NB; i++) {
+        const int c = c0 + lane + 32 * i;
+        fused_compute<PREC, RULE, DC, DV>(C, P, c, sbit(c), g[i], CVn);
+      }
+    } else {
+      for (int c = c0 + lane; c < C.m && c < c0 + CH; c += 32) {
+        FusedIn<PREC, DC, DV> g;
+        fused_gather<PREC, DC, DV>(C, c, CVp, g);
+        fused_compute<PREC, RULE, DC, DV>(C, P, c, sbit(c), g, CVn);
+      }
+    }
+  }
+}
+
 // Degree pairs with a fused sweep: 2D toric (4,2), 3D point (6,2), membrane (4,4),
 // bivariate bicycle (6,3), periodic chain (2,2).
 __device__ __forceinline__ bool fused_ok(const DevCode &C) {
@@ -570,7 +615,7 @@ __device__ __forceinline__ bool fused_ok(const DevCode &C) {
 template <int PREC, int RULE, bool SMEM, int DC, int DV, class SBit>
 __device__ __noinline__ void fused_run(int rank, int size, const DevCode &C, const DevParams &P,
                                        SBit sbit, const typename MT<PREC>::T *CVp,
-                                       typename MT<PREC>::T *CVn) {
+                                       typename MT<PREC>::T *CVn, int32_t *work) {
   using T = typename MT<PREC>::T;
   if (SMEM) {
     extern __shared__ __align__(16) uint8_t lim_dyn_smem[];
@@ -579,18 +624,19 @@ __device__ __noinline__ void fused_run(int rank, int size, const DevCode &C, con
   }
   constexpr int NP = DC * (DV - 1);
   constexpr int NB = SMEM ? 2 : (NP <= 4 ? 4 : (NP <= 6 ? 2 : 1));
-  fused_loop<PREC, RULE, DC, DV, NB>(rank, size, C, P, sbit, CVp, CVn);
+  if (work && !SMEM) fused_loop_dyn<PREC, RULE, DC, DV, NB>(work, C, P, sbit, CVp, CVn);
+  else fused_loop<PREC, RULE, DC, DV, NB>(rank, size, C, P, sbit, CVp, CVn);
 }
 
 template <int PREC, int RULE, bool SMEM, class SBit>
 __device__ __forceinline__ void fused_pass(int rank, int size, const DevCode &C, const DevParams &P,
                                            SBit sbit, const typename MT<PREC>::T *CVp,
-                                           typename MT<PREC>::T *CVn) {
-  if (C.dc_u == 4 && C.dv_u == 2) fused_run<PREC, RULE, SMEM, 4, 2>(rank, size, C, P, sbit, CVp, CVn);
-  else if (C.dc_u == 6 && C.dv_u == 2) fused_run<PREC, RULE, SMEM, 6, 2>(rank, size, C, P, sbit, CVp, CVn);
-  else if (C.dc_u == 4 && C.dv_u == 4) fused_run<PREC, RULE, SMEM, 4, 4>(rank, size, C, P, sbit, CVp, CVn);
-  else if (C.dc_u == 6 && C.dv_u == 3) fused_run<PREC, RULE, SMEM, 6, 3>(rank, size, C, P, sbit, CVp, CVn);
-  else fused_run<PREC, RULE, SMEM, 2, 2>(rank, size, C, P, sbit, CVp, CVn);
+                                           typename MT<PREC>::T *CVn, int32_t *work) {
+  if (C.dc_u == 4 && C.dv_u == 2) fused_run<PREC, RULE, SMEM, 4, 2>(rank, size, C, P, sbit, CVp, CVn, work);
+  else if (C.dc_u == 6 && C.dv_u == 2) fused_run<PREC, RULE, SMEM, 6, 2>(rank, size, C, P, sbit, CVp, CVn, work);
+  else if (C.dc_u == 4 && C.dv_u == 4) fused_run<PREC, RULE, SMEM, 4, 4>(rank, size, C, P, sbit, CVp, CVn, work);
+  else if (C.dc_u == 6 && C.dv_u == 3) fused_run<PREC, RULE, SMEM, 6, 3>(rank, size, C, P, sbit, CVp, CVn, work);
+  else fused_run<PREC, RULE, SMEM, 2, 2>(rank, size, C, P, sbit, CVp, CVn, work);
 }
 
 struct SBitWords {  // s~ from bit-packed words

@@ -119,3 +119,29 @@ def gpu_runner(ctx, prm, seed: int) -> Callable:
         tal, _ = lim.run_batch(ctx, points, prm, seed)
         return tal
     return run
+
+
+def run_until(runner: Callable, points: Sequence, batch_shots: int, max_shots: int,
+              max_failures: int) -> np.ndarray:
+    """Monte Carlo estimate per point with the stopping rule of the paper's
+    numerics: keep adding batches of ``batch_shots`` fresh shots to a point until
+    it has ``max_shots`` shots or ``max_failures`` logical failures, whichever
+    comes first (Sec. S4: 500,000 shots or 100 logical errors).  Points still
+    running are batched together.  Returns the per-point tallies."""
+    total = np.zeros(len(points), dtype=TALLY_DTYPE)
+    done = np.zeros(len(points), dtype=bool)
+    b = 0
+    while not done.all():
+        idx = [i for i in range(len(points)) if not done[i]]
+        window = []
+        for i in idx:
+            pt = points[i]
+            n = min(batch_shots, max_shots - int(total[i]["shots"]))
+            window.append((pt[0], pt[1], n, pt[3] + b * batch_shots, pt[4]) + tuple(pt[5:]))
+        t = runner(window)
+        for j, i in enumerate(idx):
+            acc = total[i:i + 1].view(np.int64) + t[j:j + 1].view(np.int64)
+            total[i] = acc.view(TALLY_DTYPE)[0]
+            done[i] = total[i]["shots"] >= max_shots or total[i]["failures"] >= max_failures
+        b += 1
+    return total

@@ -130,3 +130,12 @@ def test_checkpoint_resume_is_exact(tmp_path):
     assert np.array_equal(resumed.view(np.int64), full.view(np.int64))
     with pytest.raises(ValueError):
         D.load_checkpoint(ck, "other-run", len(pts))
+
+
+def test_adaptive_stopping_rule():
+    """Sec. S4: a point stops at max_shots shots or max_failures failures."""
+    pts = [(_Code(I.toric2d(4)), 0.2, 0, 0, 0), (_Code(I.toric2d(4)), 0.01, 0, 0, 1)]
+    tot = D.run_until(oracle_runner(3), pts, batch_shots=16, max_shots=96, max_failures=10)
+    hi, lo = tot[0], tot[1]
+    assert hi["failures"] >= 10 and hi["shots"] < 96 and hi["shots"] % 16 == 0
+    assert lo["shots"] == 96 and lo["failures"] < 10
