@@ -225,6 +225,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--smem-cap", type=int, default=0, help="max shared memory per block in bytes (0 automatic, <0 all that fits)")
     ap.add_argument("--phases", action="store_true", help="report the kernel's per-phase cycle shares")
     ap.add_argument("--autotune", action="store_true", help="pick the launch shape with lim_autotune")
     ap.add_argument("--print-source-hash", action="store_true")
@@ -261,6 +262,7 @@ def main():
     prm.block_threads = args.block_threads
     prm.blocks_per_sm = args.blocks_per_sm
     prm.profile = 1 if args.phases else 0
+    prm.smem_cap = args.smem_cap
     # weak scaling: every rank runs its own disjoint shot ids of every point
     def step_points(step):
         base = (step * world + rank) * args.shots
@@ -273,7 +275,8 @@ def main():
         best.profile = prm.profile
         prm = best
         tuned = {"variant": int(prm.variant), "block_threads": int(prm.block_threads),
-                 "blocks_per_sm": int(prm.blocks_per_sm), "sample_rate": rate}
+                 "blocks_per_sm": int(prm.blocks_per_sm), "smem_cap": int(prm.smem_cap),
+                 "sample_rate": rate}
     batch = L.Batch(ctx, step_points(0), prm, records=True)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 126 MB L2

@@ -118,6 +118,12 @@ typedef struct {
   int32_t block_threads;   /* 0 = library default                                   */
   int32_t blocks_per_sm;   /* 0 = as many as fit                                    */
   int32_t profile;         /* 1: accumulate clock cycles per phase into the tally   */
+  int32_t smem_cap;        /* CTA variant: max shared memory per block in bytes;    */
+                           /* 0 = automatic (160 KB when some code of the batch keeps */
+                           /* its messages in HBM, else all that fits), < 0 = all    */
+                           /* that fits.  A smaller cap leaves more of the SM's      */
+                           /* unified L1/shared array to the L1 cache, which serves  */
+                           /* the codes whose messages stay in HBM                   */
 } lim_params;
 
 typedef struct {

@@ -37,6 +37,7 @@ void set_error(const std::string &msg) { g_last_error = msg; }
 namespace {
 
 constexpr size_t kWsHeader = 4096;  // queue counter + a tally used by lim_trace
+constexpr size_t kStreamSmemCap = 160 * 1024;  // shared memory per block when a code streams from HBM
 
 int cuda_fail(cudaError_t err, const char *what) {
   set_error(std::string(what) + ": " + cudaGetErrorString(err));
@@ -191,7 +192,18 @@ int make_plan(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_param
     size_t cap = (size_t)ctx->smem_per_sm / target;
     cap = cap > 2048 ? cap - 2048 : cap;
     cap = std::min(cap, (size_t)ctx->smem_optin);
+    if (prm->smem_cap > 0) cap = std::min(cap, (size_t)prm->smem_cap);
     if (max_bits > cap) return bad(LIM_E_UNSUPPORTED, "bit vectors of a code exceed shared memory");
+    if (prm->smem_cap == 0) {
+      // A code whose messages do not fit streams them from HBM through L1 every
+      // sweep; a block holding (nearly) all of shared memory leaves L1 ~30 KB and
+      // those codes thrash it.  Then cap shared memory at 160 KB, which leaves
+      // L1 ~90 KB (on the 2D toric mix caps of 96, 128 and 160 KB ran alike, all
+      // 16% faster than no cap).
+      bool streams = false;
+      for (const CodeLayout &l : lay) streams |= l.bits_bytes + l.msg_bytes > cap;
+      if (streams) cap = std::max(max_bits, std::min(cap, kStreamSmemCap));
+    }
     size_t team = max_bits, slot = 0;
     for (size_t i = 0; i < pl.codes.size(); i++) {
       const CodeLayout &l = lay[i];
@@ -716,12 +728,13 @@ int lim_autotune(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_pa
       if (sample_ticks > 0) p.tick_budget = std::min(T, sample_ticks);
     }
     struct Shape {
-      int variant, block, bpsm;
+      int variant, block, bpsm, cap;
     };
-    const Shape shapes[] = {{LIM_VARIANT_CTA, 1024, 1}, {LIM_VARIANT_CTA, 512, 2},
-                            {LIM_VARIANT_CTA, 512, 1},  {LIM_VARIANT_CTA, 256, 4},
-                            {LIM_VARIANT_WARP, 256, 0}, {LIM_VARIANT_WARP, 512, 0},
-                            {LIM_VARIANT_WARP, 128, 0}};
+    const Shape shapes[] = {{LIM_VARIANT_CTA, 1024, 1, 0},        {LIM_VARIANT_CTA, 1024, 1, -1},
+                            {LIM_VARIANT_CTA, 1024, 1, 48 << 10}, {LIM_VARIANT_CTA, 512, 2, 0},
+                            {LIM_VARIANT_CTA, 512, 1, 0},         {LIM_VARIANT_CTA, 256, 4, 0},
+                            {LIM_VARIANT_WARP, 256, 0, 0},        {LIM_VARIANT_WARP, 512, 0, 0},
+                            {LIM_VARIANT_WARP, 128, 0, 0}};
     double best_rate = -1;
     lim_params best_p = *prm;
     void *ws = nullptr;
@@ -738,6 +751,7 @@ int lim_autotune(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_pa
       p.variant = sh.variant;
       p.block_threads = sh.block;
       p.blocks_per_sm = sh.bpsm;
+      p.smem_cap = sh.cap;
       size_t need = 0;
       if (lim_workspace_size(ctx, sample.data(), npts, &p, &need) != LIM_OK) continue;  // shape does not fit
       if (need > ws_bytes) {

@@ -57,7 +57,7 @@ class Params(ctypes.Structure):
                 ("ring_prob", ctypes.c_double), ("tick_budget", ctypes.c_int32),
                 ("gauge_on_move", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("profile", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("smem_cap", ctypes.c_int32)]
 
 
 class Point(ctypes.Structure):
@@ -128,11 +128,12 @@ def check(st: int, what: str = "") -> None:
 
 def params(rule="minsum", feedback="check_move", precision="f32", quant_scale=2.0 ** -6, q=0.05,
            clamp=1000.0, tau=0.1, dt_tick=0.1, sweeps_per_tick=1, ring_prob=-1.0, tick_budget=32,
-           gauge_on_move=0, variant="auto", block_threads=0, blocks_per_sm=0, profile=0) -> Params:
+           gauge_on_move=0, variant="auto", block_threads=0, blocks_per_sm=0, profile=0,
+           smem_cap=0) -> Params:
     return Params(RULE[rule], FEEDBACK[feedback], PREC[precision], float(quant_scale), float(q),
                   float(clamp), float(tau), float(dt_tick), int(sweeps_per_tick), float(ring_prob),
                   int(tick_budget), int(gauge_on_move), VARIANT[variant], int(block_threads),
-                  int(blocks_per_sm), int(profile))
+                  int(blocks_per_sm), int(profile), int(smem_cap))
 
 
 def prec_name(prm: Params) -> str:
