@@ -50,18 +50,17 @@ def workload(name: str, shots: int, sizes=None, ps=None):
         if ps and not any(abs(p - float(x)) < 1e-9 for x in ps):
             continue
         pts.append(dict(family=fam, size=size, p=p, point_id=pid, shots=shots,
-                        T=I.tick_budget(w["budget"], size)))
+                        T=I.tick_budget(w["budget"], size, w["dt_tick"])))
     # most expensive points first: the queue hands out work in this order
     pts.sort(key=lambda d: (-I.make_code(d["family"], d["size"]).E * d["T"], -d["p"]))
     return w, pts
 
 
 def lib_params(L, w, name, prec, variant="auto"):
-    if name == "rep2000_p045":
-        return L.params(feedback="bit_discrete", precision=prec, q=w["q"], clamp=w["clamp"],
-                        tick_budget=8001, variant=variant)
     qs = 0.25 if prec == "i8" else 2 ** -6
-    return L.params(precision=prec, quant_scale=qs, q=w["q"], clamp=w["clamp"], tau=w["tau"],
+    return L.params(rule=w.get("rule", "minsum"), feedback=w.get("feedback", "check_move"),
+                    precision=prec, quant_scale=qs,
+                    q=w["q"], clamp=w["clamp"], tau=w["tau"],
                     dt_tick=w["dt_tick"], sweeps_per_tick=w["K"], tick_budget=w.get("T", 0) or 1,
                     variant=variant)
 
@@ -166,7 +165,9 @@ def cpu_baseline(name: str, prec: str, seconds: float = 15.0, threads: int = 0):
             for d in jobs:
                 c, oc = codes[(d["family"], d["size"])]
                 op = O.params(precision=prec if prec in ("f32", "f16", "bf16", "i16", "i8") else "f64",
-                              quant_scale=2 ** -6, q=w["q"], clamp=w["clamp"], tau=w["tau"],
+                              rule=w.get("rule", "minsum"), feedback=w.get("feedback", "check_move"),
+                              quant_scale=0.25 if prec == "i8" else 2 ** -6,
+                              q=w["q"], clamp=w["clamp"], tau=w["tau"],
                               dt_tick=w["dt_tick"], sweeps_per_tick=w["K"], tick_budget=d["T"])
                 futs.append((c, ex.submit(O.run_shots, oc, op, d["p"], 0, d["point_id"], rnd, 1)))
             for c, f in futs:
@@ -341,8 +342,9 @@ def main():
             "config": {"workload": args.workload, "codes": f"{w['family']} sizes {w['sizes']}",
                        "points": len(pts), "shots_per_point_per_step": args.shots,
                        "shots_per_step": shots // max(1, args.steps) // world,
-                       "rule": "minsum",
-                       "feedback": "bit_discrete" if args.workload == "rep2000_p045" else "check_move",
+                       "rule": w.get("rule", "minsum"),
+                       "feedback": w.get("feedback", "check_move"),
+                       "tau": w["tau"], "dt_tick": w["dt_tick"],
                        "sweeps_per_tick": w.get("K", 1), "tick_budget": w["budget"],
                        "variant": args.variant,
                        "l2": "flushed between steps (256 MiB write, outside the timed window)",

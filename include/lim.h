@@ -62,6 +62,13 @@ extern "C" {
 /* Feedback rule. */
 #define LIM_FB_CHECK_MOVE 0   /* continuous machine: Algorithm 1, Evidence + LocalMove */
 #define LIM_FB_BIT_DISCRETE 1 /* discrete machine: f_v = 1[L_v > 0], Eq. 3-4, gauge */
+/* Ordinary BP decoding (fixed syndrome, hard decision after every iteration, stop
+ * when the decision reproduces the syndrome; a tie L_v = 0 keeps the previous
+ * decision) is, by the Lemma mapping the discrete machine to ordinary BP, the
+ * discrete machine itself: its records are the decoder's (t_clr = the iteration
+ * that reproduced the syndrome, moves = decision changes, failed) and the final
+ * residual from lim_final_words is e0 + ehat. */
+#define LIM_FB_BP_DECODER LIM_FB_BIT_DISCRETE
 
 /* Message storage precision (arithmetic: binary32 for the floating modes,
  * int32 for the integer modes; qubit and syndrome decisions are exact GF(2)). */

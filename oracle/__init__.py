@@ -99,6 +99,9 @@ def lib() -> ctypes.CDLL:
         L.or_run_shots.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), ctypes.c_double,
                                    ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                    ctypes.c_uint32, vp]
+        L.or_bp_decode.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), ctypes.c_double,
+                                   ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                   ctypes.POINTER(Record), vp]
         L.or_bp_sweeps.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), vp, vp, vp, vp,
                                    vp, vp, ctypes.c_int32]
         L.or_readout.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), vp, vp, vp]
@@ -168,6 +171,27 @@ def noise(code: OracleCode, p: float, seed: int, point: int, shot: int):
     s = np.zeros(max(code.m, 1), dtype=np.uint8)
     _check(lib().or_noise(ctypes.byref(code.struct), p, seed, point, shot, _ptr(e), _ptr(s)), "noise")
     return e, s[:code.m]
+
+
+def bp_decode(code: OracleCode, prm: Params, p: float, seed: int, point: int, shot: int):
+    """Ordinary BP decoding of one shot (fixed syndrome, hard decision after every
+    iteration, stop when it reproduces the syndrome): (record dict, ehat bytes)."""
+    rec = Record()
+    ehat = np.zeros(code.n, dtype=np.uint8)
+    _check(lib().or_bp_decode(ctypes.byref(code.struct), ctypes.byref(prm), p, seed, point, shot,
+                              ctypes.byref(rec), _ptr(ehat)), "bp_decode")
+    return {f: getattr(rec, f) for f, _ in Record._fields_}, ehat
+
+
+def bp_decode_shots(code: OracleCode, prm: Params, p: float, seed: int, point: int, shot0: int,
+                    nshots: int) -> np.ndarray:
+    """Records (RECORD_DTYPE) of ordinary BP decoding for shots shot0 .. shot0+nshots-1."""
+    out = np.zeros(nshots, dtype=RECORD_DTYPE)
+    for i in range(nshots):
+        r, _ = bp_decode(code, prm, p, seed, point, shot0 + i)
+        for f in RECORD_DTYPE.names:
+            out[i][f] = r[f]
+    return out
 
 
 def run_shot(code: OracleCode, prm: Params, p: float, seed: int, point: int, shot: int,

@@ -694,6 +694,84 @@ done:
   return st;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Ordinary BP decoding: fixed syndrome, no gauge, hard decision per iteration. */
+/* ------------------------------------------------------------------------- */
+int or_bp_decode(const or_code *code, const or_params *prm, double p, uint64_t seed,
+                 uint32_t point, uint32_t shot, or_record *rec, uint8_t *ehat_out) {
+  if (!rec) return OR_E_INVAL;
+  wk w;
+  int st = setup_wk(prm, &w);
+  if (st != OR_OK) return st;
+  graph g;
+  st = graph_build(code, &g);
+  if (st != OR_OK) return st;
+  int n = g.n, m = g.m;
+  size_t E = (size_t)(g.E > 0 ? g.E : 1), M = (size_t)(m > 0 ? m : 1);
+  int dmax = max_check_degree(&g);
+  uint8_t *e0 = calloc((size_t)n, 1), *ehat = calloc((size_t)n, 1);
+  uint8_t *s = calloc(M, 1), *s_hat = calloc(M, 1);
+  double *pi = malloc((size_t)n * sizeof(double)), *L = malloc((size_t)n * sizeof(double));
+  double *cv = calloc(E, sizeof(double)), *vc = calloc(E, sizeof(double));
+  double *cn = calloc(E, sizeof(double)), *vn = calloc(E, sizeof(double));
+  double *xb = malloc((size_t)(dmax + 1) * sizeof(double));
+  if (!e0 || !ehat || !s || !s_hat || !pi || !L || !cv || !vc || !cn || !vn || !xb) {
+    st = OR_E_NOMEM;
+    goto done;
+  }
+  for (int v = 0; v < n; v++) pi[v] = w.pi0;
+  noise(&g, p, seed, point, shot, e0, s);
+
+  or_record r = {-1, 0, 1, 0, 0, 0};
+  if (all_zero(s, m)) {
+    r.t_clr = 0;
+    r.converged = 1;
+  } else {
+    for (int i = 1; i <= prm->tick_budget; i++) {
+      r.ticks = i;
+      readout(&w, &g, pi, cv, L); /* beliefs from the messages after i-1 sweeps */
+      for (int v = 0; v < n; v++) {
+        uint8_t d = L[v] > 0 ? 1 : (L[v] < 0 ? 0 : ehat[v]);
+        if (d != ehat[v]) {
+          ehat[v] = d;
+          r.moves++;
+        }
+      }
+      syndrome(&g, ehat, s_hat);
+      if (memcmp(s_hat, s, (size_t)m) == 0) {
+        r.t_clr = i;
+        r.converged = 1;
+        break;
+      }
+      if (i == prm->tick_budget) break;
+      for (int k = 0; k < prm->sweeps_per_tick; k++) {
+        sweep(&w, &g, s, pi, cv, vc, cn, vn, xb);
+        double *tmp = cv; cv = cn; cn = tmp;
+        tmp = vc; vc = vn; vn = tmp;
+        r.sweeps++;
+      }
+    }
+  }
+  /* The decoder's output is ehat; the residual e0 + ehat has zero syndrome when
+   * converged and fails iff it anticommutes with an X-logical. */
+  if (r.converged) {
+    r.failed = 0;
+    for (int j = 0; j < code->k; j++) {
+      int par = 0;
+      for (int v = 0; v < n; v++) par ^= (e0[v] ^ ehat[v]) & code->logicals[(size_t)j * n + v];
+      if (par) r.failed = 1;
+    }
+  }
+  if (ehat_out) memcpy(ehat_out, ehat, (size_t)n);
+  *rec = r;
+  st = OR_OK;
+done:
+  free(e0); free(ehat); free(s); free(s_hat); free(pi); free(L);
+  free(cv); free(vc); free(cn); free(vn); free(xb);
+  graph_free(&g);
+  return st;
+}
+
 int or_run_shots(const or_code *code, const or_params *prm, double p, uint64_t seed,
                  uint32_t point, uint32_t shot0, uint32_t nshots, or_record *records) {
   for (uint32_t i = 0; i < nshots; i++) {

@@ -21,6 +21,10 @@
  *   end     logical check: failure iff not converged, or the residual has odd
  *           overlap with an X-logical                     (decoding criteria (1)-(2))
  *
+ * Also: ordinary BP decoding (fixed syndrome, hard decision after every
+ * iteration), the decoder the machine is compared with and, by the Lemma
+ * mapping the discrete machine to ordinary BP, its bit-centric counterpart.
+ *
  * Precision modes.  OR_PREC_F64 is the paper's arithmetic in double precision.
  * OR_PREC_F32/F16/BF16 perform every addition, subtraction and multiplication
  * correctly rounded to binary32 and round stored messages to the storage format
@@ -36,6 +40,9 @@
  * forms of code parameters, an independent Philox implementation).  The one
  * quantity without such a pin is the absolute logical error rate of the
  * check-centric machine (the paper prints no value for it): parity unpinned.
+ * (The CUDA path, equal to this oracle shot by shot, reproduces the thresholds
+ * of Table S1 with the paper's rule and discretisation; that check runs on the
+ * GPU only, at sample sizes this oracle cannot reach in a test.)
  */
 #ifndef LIM_ORACLE_H
 #define LIM_ORACLE_H
@@ -129,6 +136,20 @@ int or_run_from(const or_code *code, const or_params *prm, const uint8_t *e0, ui
 /* Many shots (single thread), records[i] for shot shot0+i. */
 int or_run_shots(const or_code *code, const or_params *prm, double p, uint64_t seed,
                  uint32_t point, uint32_t shot0, uint32_t nshots, or_record *records);
+
+/* Ordinary BP decoding, the comparison decoder (the "traditional" use of BP set
+ * out after Eq. 2): flooding Jacobi sweeps of Eq. 1-2 (relaxed and clamped as in
+ * or_run_shot) on the fixed syndrome s = H_X e0 with fixed priors; after every
+ * iteration a hard decision ehat_v = argmax_b Pr_BP(e_v = b | s), i.e. 1 if
+ * L_v > 0 and 0 if L_v < 0 (a tie L_v = 0 keeps the previous decision, initially
+ * 0); decoding stops at the first iteration whose decision reproduces the
+ * syndrome, H_X ehat = s.  Iteration i reads the messages after i-1 sweeps, so
+ * rec->t_clr is that i (0 when s = 0), rec->moves counts decision changes,
+ * rec->failed = not converged, or e0 + ehat anticommutes with an X-logical.
+ * prm->feedback and prm->gauge_on_move are ignored: no gauge, no feedback.
+ * ehat_out ([n] bytes) may be NULL. */
+int or_bp_decode(const or_code *code, const or_params *prm, double p, uint64_t seed,
+                 uint32_t point, uint32_t shot, or_record *rec, uint8_t *ehat_out);
 
 /* K Jacobi sweeps on a fixed syndrome s (bytes) and priors pi ([n], NULL = uniform
  * log(q/(1-q))), messages by edge id (CSR order).  Values are in LLR units for the

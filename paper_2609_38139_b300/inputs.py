@@ -400,7 +400,8 @@ WORKLOADS = {
                              budget="4L"),
     # open repetition chain d=2000, p=0.45, discrete (bit-centric) machine.
     "rep2000_p045": dict(family="rep", sizes=[2000], p=[0.45], shots=1000,
-                         q=0.05, clamp=1000.0, budget="4d+1"),
+                         q=0.05, clamp=1000.0, tau=0.1, dt_tick=0.1, K=1, budget="4d+1",
+                         feedback="bit_discrete"),
     # batched 2D toric sweep, L in {16,32,64,128}, 11 p points in 0.02-0.12.
     "toric2d_sweep": dict(family="toric2d", sizes=[16, 32, 64, 128], p=p_grid(0.02, 0.12, 11),
                           shots=100000, q=0.05, clamp=1000.0, tau=0.1, dt_tick=0.1, K=1,
@@ -417,6 +418,47 @@ WORKLOADS = {
     "bb_mixed": dict(family="bb", sizes=[(6, 6), (15, 3), (12, 6)], p=p_grid(0.01, 0.08, 9),
                      shots=1000000 // 27, q=0.05, clamp=1000.0, tau=0.1, dt_tick=0.1, K=1,
                      budget=10000),
+    # Table S1 discretisations (fine dt, relaxation alpha = dt/tau, budget t_max/dt) with the
+    # paper's check rule (sum-product, Eq. 2) at the smaller sizes of each family; t_max = 1000
+    # also for the families the table leaves open.
+    "toric2d_fine_dt": dict(family="toric2d", sizes=[8, 12, 16, 24], p=p_grid(0.04, 0.10, 7),
+                            shots=100000, q=0.05, clamp=1000.0, tau=0.1, dt_tick=0.001, K=1,
+                            budget="t_max=1000", rule="sumproduct"),
+    # The benchmark's coarse discretisation (dt = tau, one undamped sweep per tick) on the
+    # same sizes, p grid and decoder time t_max, to compare the LER trends with the above.
+    "toric2d_coarse_dt": dict(family="toric2d", sizes=[8, 12, 16, 24], p=p_grid(0.04, 0.10, 7),
+                              shots=100000, q=0.05, clamp=1000.0, tau=0.1, dt_tick=0.1, K=1,
+                              budget="t_max=1000", rule="sumproduct"),
+    # Fig. S1(c-d): the same with relaxation time tau = 0.15 and 0.2.
+    "toric2d_fine_dt_tau015": dict(family="toric2d", sizes=[8, 12, 16], p=p_grid(0.04, 0.10, 7),
+                                   shots=100000, q=0.05, clamp=1000.0, tau=0.15, dt_tick=0.001,
+                                   K=1, budget="t_max=1000", rule="sumproduct"),
+    "toric2d_fine_dt_tau02": dict(family="toric2d", sizes=[8, 12, 16], p=p_grid(0.04, 0.10, 7),
+                                  shots=100000, q=0.05, clamp=1000.0, tau=0.2, dt_tick=0.001,
+                                  K=1, budget="t_max=1000", rule="sumproduct"),
+    "toric3d_point_fine_dt": dict(family="toric3d_point", sizes=[4, 6, 8, 10],
+                                  p=p_grid(0.01, 0.03, 5), shots=100000, q=0.05, clamp=1000.0,
+                                  tau=0.1, dt_tick=0.001, K=1, budget="t_max=1000",
+                                  rule="sumproduct"),
+    # membrane sizes d in {4, 6, 8, 10, 12} as in Fig. 4(a)
+    "toric3d_membrane_fine_dt": dict(family="toric3d_membrane", sizes=[4, 6, 8, 10, 12],
+                                     p=p_grid(0.10, 0.22, 7), shots=100000, q=0.125,
+                                     clamp=1000.0, tau=0.1, dt_tick=0.01, K=1,
+                                     budget="t_max=1000", rule="sumproduct"),
+    # the paper's BB sequence (l, m) in {(6,6), (12,6), (18,9), (24,12)} (Fig. 4(c))
+    "bb_fine_dt": dict(family="bb", sizes=[(6, 6), (12, 6), (18, 9), (24, 12)],
+                       p=p_grid(0.02, 0.08, 7), shots=100000, q=0.05, clamp=1000.0, tau=0.1,
+                       dt_tick=0.01, K=1, budget="t_max=1000", rule="sumproduct"),
+    # Fig. 2: discrete machine on open repetition chains d in {20, 40, 80, 160}.
+    "rep_fig2": dict(family="rep", sizes=[20, 40, 80, 160], p=p_grid(0.10, 0.50, 9),
+                     shots=100000, q=0.05, clamp=1000.0, tau=0.1, dt_tick=0.1, K=1,
+                     budget="4d+1", feedback="bit_discrete"),
+    # Ordinary BP decoding of the 2D toric code: flooding min-sum with a hard decision after
+    # every iteration, stopping when it reproduces the syndrome.  By the Lemma mapping the
+    # discrete machine to ordinary BP this is the bit-centric machine run on the toric code.
+    "toric2d_bp_decoder": dict(family="toric2d", sizes=[8, 16, 32, 64], p=p_grid(0.01, 0.10, 10),
+                               shots=100000, q=0.05, clamp=1000.0, tau=0.1, dt_tick=0.1, K=1,
+                               budget=100, feedback="bit_discrete"),
 }
 
 
@@ -435,10 +477,14 @@ def make_code(family: str, size) -> Code:
     raise ValueError(family)
 
 
-def tick_budget(spec, size) -> int:
+def tick_budget(spec, size, dt_tick: float = 0.1) -> int:
+    """Ticks a shot may run: an integer, a multiple of the code size, or
+    ``"t_max=<time>"`` (the paper's maximum decoder time over the tick length)."""
     b = spec
     if isinstance(b, int):
         return b
+    if b.startswith("t_max="):
+        return int(round(float(b[6:]) / dt_tick))
     if b == "4L":
         return 4 * int(size)
     if b == "40L":

@@ -220,6 +220,62 @@ def test_relaxed_multi_sweep_and_gauge(L, ctx):
     _batch_vs_oracle(L, ctx, I.toric3d_membrane(3), prm, 0.05, 80)
 
 
+@pytest.mark.parametrize("maker,prec,q,dt,p,variant", [
+    (lambda: I.toric2d(6), "f32", 0.05, 0.001, 0.06, "warp"),
+    (lambda: I.toric2d(8), "f32", 0.05, 0.001, 0.08, "cta"),
+    (lambda: I.toric3d_point(3), "f16", 0.05, 0.001, 0.03, "cta"),
+    (lambda: I.toric3d_membrane(3), "i16", 0.125, 0.01, 0.12, "warp"),
+    (lambda: I.bb_code(6, 6), "i8", 0.05, 0.01, 0.05, "warp"),
+])
+def test_fine_dt_trajectories(L, ctx, maker, prec, q, dt, p, variant):
+    """Table S1 discretisations: relaxation alpha = dt/tau (0.01 or 0.1), ring
+    probability 1 - exp(-dt) per tick, and a budget of 100 time units (1e4 or 1e5
+    ticks); every shot's trajectory summary equals the oracle's."""
+    prm = L.params(precision=prec, quant_scale=0.25 if prec == "i8" else 2 ** -6, q=q, tau=0.1,
+                   dt_tick=dt, tick_budget=int(round(100 / dt)), variant=variant)
+    _batch_vs_oracle(L, ctx, maker(), prm, p, 16, finals=False)
+
+
+@pytest.mark.parametrize("prec", ["f32", "i16"])
+def test_bp_decoder_row_matches_oracle_decoder(L, ctx, prec):
+    """Ordinary BP decoding of the 2D toric code, the comparison decoder: the
+    bit-centric machine on the GPU against the oracle's gauge-free BP decoder
+    (fixed syndrome, hard decision after every iteration), shot by shot, final
+    residual e0 + ehat included."""
+    code = I.toric2d(8)
+    prm = L.params(feedback="bit_discrete", precision=prec, tick_budget=100)
+    lc = ctx.from_inputs(code)
+    tal, rec, fin = L.run_batch(ctx, [(lc, 0.05, 64, 0, 4)], prm, 13, e_final=True)
+    oc = O.OracleCode.from_code(code)
+    op = oracle_params(prm)
+    ora = O.bp_decode_shots(oc, op, 0.05, 13, 4, 0, 64)
+    compare_records(rec, ora, f"bp decoder {prec}")
+    e_gpu = _unpack(fin, code.n)
+    for sh in range(64):
+        _, ehat = O.bp_decode(oc, op, 0.05, 13, 4, sh)
+        e0, _ = O.noise(oc, 0.05, 13, 4, sh)
+        assert np.array_equal(e_gpu[sh], e0 ^ ehat), sh
+
+
+def test_study_runner_on_rep_fig2(L, ctx):
+    """The adaptive Monte Carlo runner on the Fig. 2 workload (d = 20): per point,
+    the failures are the shots whose initial error has a strict majority, up to
+    exact ties and non-converged shots (Theorem on the rep code)."""
+    from paper_2609_38139_b300 import study as S
+    rows = S.run_study(ctx, "rep_fig2", max_shots=256, max_failures=10 ** 9, batch_shots=128,
+                       sizes=[20])
+    assert len(rows) == 9
+    oc = O.OracleCode.from_code(I.rep_code(20))
+    for r in rows:
+        assert r["shots"] == 256
+        maj = ties = 0
+        for sh in range(256):
+            w = int(O.noise(oc, r["p"], 0, r["point_id"], sh)[0].sum())
+            maj += 2 * w > 20
+            ties += 2 * w == 20
+        assert maj <= r["failures"] <= maj + ties + r["nonconverged"], r
+
+
 def test_discrete_machine_on_a_quantum_code(L, ctx):
     prm = L.params(feedback="bit_discrete", precision="f32", tick_budget=60, tau=0, dt_tick=0)
     _batch_vs_oracle(L, ctx, I.toric2d(6), prm, 0.04, 100)

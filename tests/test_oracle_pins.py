@@ -400,6 +400,58 @@ def test_mapping_to_ordinary_bp(maker, prec, rule):
             cv, vc = O.bp_sweeps(oc, prm, s0, cv, vc, 1)
 
 
+@pytest.mark.parametrize("maker,prec,rule,tau,K", [
+    (lambda: I.rep_code(50), "f64", "minsum", 0.0, 1),
+    (lambda: I.rep_code(50, periodic=True), "f32", "sumproduct", 0.0, 1),
+    (lambda: I.toric2d(6), "f64", "minsum", 0.0, 1),
+    (lambda: I.toric2d(6), "f32", "minsum", 0.2, 2),
+    (lambda: I.toric2d(5), "i16", "minsum", 0.0, 1),
+    (lambda: I.bb_code(6, 6), "f16", "minsum", 0.0, 1),
+    (lambda: I.toric3d_membrane(3), "i8", "minsum", 0.0, 1)])
+def test_ordinary_bp_decoder_equals_discrete_machine(maker, prec, rule, tau, K):
+    """Ordinary BP decoding (fixed syndrome, hard decision after every iteration,
+    stop when H ehat = s) written without gauge or feedback, against the discrete
+    machine: by the Lemma mapping the machine to ordinary BP the machine's
+    cumulative flips are the decoder's decisions, so t_clr, convergence, failure,
+    the number of flips and the final residual e0 + ehat coincide exactly."""
+    code = maker()
+    oc = O.OracleCode.from_code(code)
+    T = 40 if code.n > 60 else 4 * code.n + 1
+    prm = O.params(rule=rule, feedback="bit_discrete", precision=prec, q=0.1, tau=tau,
+                   dt_tick=0.1 if tau else 0.0, sweeps_per_tick=K, tick_budget=T)
+    p = 0.3 if code.name.startswith("rep") else 0.06
+    conv = 0
+    for shot in range(40):
+        b, ehat = O.bp_decode(oc, prm, p, 5, 3, shot)
+        r = O.run_shot(oc, prm, p, 5, 3, shot, trace_ticks=T)
+        for f in ("t_clr", "converged", "failed", "moves", "ticks", "sweeps"):
+            assert b[f] == r[f], (shot, f, b[f], r[f])
+        e0, _ = O.noise(oc, p, 5, 3, shot)
+        assert np.array_equal(r["trace"]["e_hist"][T], e0 ^ ehat), shot
+        conv += b["converged"]
+    assert conv > 0
+
+
+def test_ordinary_bp_decoder_clears_single_errors():
+    """A single error on a long open chain (a tree, where BP is exact) is found
+    after the beliefs have crossed the chain's few hops: the decision is exactly
+    that qubit and the decoder converges."""
+    code = I.rep_code(9)
+    oc = O.OracleCode.from_code(code)
+    prm = O.params(feedback="bit_discrete", precision="f64", q=0.1, tau=0, dt_tick=0,
+                   tick_budget=40)
+    found = 0
+    for shot in range(400):
+        e0, s0 = O.noise(oc, 0.05, 9, 0, shot)
+        if int(e0.sum()) != 1:
+            continue
+        b, ehat = O.bp_decode(oc, prm, 0.05, 9, 0, shot)
+        assert b["converged"] == 1 and b["failed"] == 0
+        assert np.array_equal(ehat, e0)
+        found += 1
+    assert found >= 5
+
+
 @pytest.mark.parametrize("maker,fb,prec", [
     (lambda: I.toric2d(6), "check_move", "f64"), (lambda: I.toric3d_membrane(3), "check_move", "i16"),
     (lambda: I.bb_code(6, 6), "check_move", "f32"), (lambda: I.rep_code(30), "bit_discrete", "i8")])
