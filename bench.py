@@ -137,13 +137,15 @@ def peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def cpu_baseline(name: str, prec: str, seconds: float = 15.0, threads: int = 0):
+def cpu_baseline(name: str, prec: str, seconds: float = 15.0, threads: int = 0, rule: str = ""):
     """The oracle timed on this host's cores on a bounded sample of the workload:
     shots of every point in turn (same keyed shot ids as the GPU's step 0) until
     about ``seconds`` of wall time have passed."""
     import oracle as O
     from concurrent.futures import ThreadPoolExecutor
     w, pts = workload(name, 1)
+    if rule:
+        w = dict(w, rule=rule)
     threads = threads or (os.cpu_count() or 1)
     codes = {}
     t0 = time.perf_counter()
@@ -189,11 +191,12 @@ def run_reference(args):
         return 0
     steps = []
     for _ in range(args.warmup):
-        cpu_baseline(args.workload, args.precision, seconds=max(1.0, args.ref_seconds / 4))
+        cpu_baseline(args.workload, args.precision, seconds=max(1.0, args.ref_seconds / 4),
+                     rule=args.rule)
     t0 = time.perf_counter()
     last = None
     for _ in range(args.steps):
-        last = cpu_baseline(args.workload, args.precision, seconds=args.ref_seconds)
+        last = cpu_baseline(args.workload, args.precision, seconds=args.ref_seconds, rule=args.rule)
         steps.append(last)
     wall = time.perf_counter() - t0
     val = statistics.mean(s["value"] for s in steps)
@@ -226,6 +229,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--rule", default="", help="minsum | sumproduct (default: the workload's)")
     ap.add_argument("--smem-cap", type=int, default=0, help="max shared memory per block in bytes (0 automatic, <0 all that fits)")
     ap.add_argument("--phases", action="store_true", help="report the kernel's per-phase cycle shares")
     ap.add_argument("--autotune", action="store_true", help="pick the launch shape with lim_autotune")
@@ -254,6 +258,8 @@ def main():
     sizes = [x for x in args.sizes.split(",") if x]
     ps = [x for x in args.ps.split(",") if x]
     w, pts = workload(args.workload, args.shots, sizes, ps)
+    if args.rule:
+        w = dict(w, rule=args.rule)
     codes = {}
     for d in pts:
         key = (d["family"], d["size"])
@@ -392,7 +398,8 @@ def main():
                                "device (part of the method); records and tallies are read back"}
         line["gpu_launches"] = args.steps
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args.workload, args.precision, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.precision, args.cpu_seconds,
+                                            rule=args.rule)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -20,7 +20,7 @@ LIM_OK = 0
 STATUS = {0: "LIM_OK", 1: "LIM_E_INVAL", 2: "LIM_E_NOMEM", 3: "LIM_E_CUDA", 4: "LIM_E_TIMEOUT",
           5: "LIM_E_NOT_CSS", 6: "LIM_E_UNSUPPORTED"}
 RULE = {"minsum": 0, "sumproduct": 1}
-FEEDBACK = {"check_move": 0, "bit_discrete": 1, "bp_decoder": 1}
+FEEDBACK = {"check_move": 0, "bit_discrete": 1}
 PREC = {"f32": 1, "f16": 2, "bf16": 3, "i16": 4, "i8": 5}
 VARIANT = {"auto": 0, "cta": 1, "warp": 2, "plain": 3}
 SECTOR = {"point": 0, "membrane": 1}
@@ -130,6 +130,8 @@ def params(rule="minsum", feedback="check_move", precision="f32", quant_scale=2.
            clamp=1000.0, tau=0.1, dt_tick=0.1, sweeps_per_tick=1, ring_prob=-1.0, tick_budget=32,
            gauge_on_move=0, variant="auto", block_threads=0, blocks_per_sm=0, profile=0,
            smem_cap=0) -> Params:
+    if feedback == "bp_decoder":  # ordinary BP decoding is the discrete machine (LIM_FB_BP_DECODER)
+        feedback = "bit_discrete"
     return Params(RULE[rule], FEEDBACK[feedback], PREC[precision], float(quant_scale), float(q),
                   float(clamp), float(tau), float(dt_tick), int(sweeps_per_tick), float(ring_prob),
                   int(tick_budget), int(gauge_on_move), VARIANT[variant], int(block_threads),

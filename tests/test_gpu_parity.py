@@ -349,13 +349,48 @@ def test_ler_f32_agrees_with_fp64_oracle(L, ctx):
     assert ok, bc
 
 
-def test_sumproduct_ler_agrees_with_fp64_oracle(L, ctx):
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+def test_sumproduct_ler_agrees_with_fp64_oracle(L, ctx, prec):
     code = I.toric2d(8)
-    prm = L.params(precision="f32", rule="sumproduct", tick_budget=64)
+    prm = L.params(precision=prec, rule="sumproduct", tick_budget=64)
     _, rec = L.run_batch(ctx, [(ctx.from_inputs(code), 0.06, 600, 0, 0)], prm, 2)
     ora = oracle_point(code, prm, 0.06, 2, 0, 0, 600, precision="f64")
     ok, bc = paired_ok(rec["failed"], ora["failed"])
     assert ok, bc
+
+
+# storage unit roundoff of each format (round to nearest: half an ulp, relative)
+UNIT_ROUNDOFF = {"f32": 2.0 ** -24, "f16": 2.0 ** -11, "bf16": 2.0 ** -8}
+
+
+@pytest.mark.parametrize("cname", ["toric2d_6", "bb_6_6", "point_3"])
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+@pytest.mark.parametrize("relaxed", [False, True])
+def test_sumproduct_sweeps_reduced_precision(L, ctx, cname, prec, relaxed):
+    """Sum-product with 16-bit storage against FP64 on the same stored inputs: each
+    output is the FP64 value up to one rounding to the storage format (relative u)
+    plus the binary32 arithmetic before it (1e-5 max(1, |m|))."""
+    code = CODES[cname]()
+    lc = ctx.from_inputs(code)
+    prm = L.params(precision=prec, rule="sumproduct", clamp=40.0, tau=0.1,
+                   dt_tick=0.03 if relaxed else 0.1)
+    rng = np.random.default_rng(17)
+    B = 6
+    s, cv, vc = _random_state(rng, code, prec, B, 4.0)
+    cvo, vco = L.bp_sweeps(lc, prm, torch.from_numpy(s).cuda(), _to_dev(L, prm, cv), _to_dev(L, prm, vc), 1)
+    cvo = cvo.double().cpu().numpy()
+    vco = vco.double().cpu().numpy()
+    oc = O.OracleCode.from_code(code)
+    op = oracle_params(prm, precision="f64")
+    u = UNIT_ROUNDOFF[prec]
+    for b in range(B):
+        rc, rv = O.bp_sweeps(oc, op, s[b], cv[b], vc[b], 1)
+        for got, ref in ((cvo[b], rc), (vco[b], rv)):
+            tol = u * np.abs(ref) + 1e-5 * np.maximum(1.0, np.abs(ref))
+            assert np.all(np.abs(got - ref) <= tol), (b, np.max(np.abs(got - ref) - tol))
+        # and the oracle's own 16-bit mode (FP64 value rounded once) agrees to one ulp
+        rc16, _ = O.bp_sweeps(oc, oracle_params(prm), s[b], cv[b], vc[b], 1)
+        assert np.all(np.abs(cvo[b] - rc16) <= 2 * u * np.abs(rc16) + 1e-6), b
 
 
 @pytest.mark.parametrize("L_,p,shots", [(128, 0.02, 3), (128, 0.12, 1), (64, 0.08, 3)])
