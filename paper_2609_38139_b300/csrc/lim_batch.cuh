@@ -24,8 +24,8 @@ struct TeamCtl {
   int32_t err;
   uint32_t logmask; // parities of e with the X-logicals
   int32_t t_clr, converged, ticks, sweeps, vc_sel, done;
-  int32_t work;     // chunk counter of the dynamically distributed sweep
-  int32_t pad[2];
+  int32_t work[2];  // chunk counters of the dynamically distributed sweep, by tick parity
+  int32_t pad;
 };
 static_assert(sizeof(TeamCtl) == 64, "TeamCtl layout");
 
@@ -33,7 +33,7 @@ LIM_HD inline size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct Layout {
   // offsets inside the team's shared memory (or the plain path's HBM slot)
-  uint32_t e, s, s0, sg, smem_free;
+  uint32_t e, s, s0, sg, tb, smem_free;
   // offsets inside the message block and the per-check scratch block
   uint32_t cv, vc0, vc1, msg_bytes;
   uint32_t cstate, cprio, ctgt, clist, chk_bytes;
@@ -46,7 +46,8 @@ __device__ __forceinline__ Layout layout(const DevCode &C, int prec) {
   L.s = L.e + 4 * C.nw;
   L.s0 = L.s + 4 * C.mw;
   L.sg = L.s0 + 4 * C.mw;
-  L.smem_free = (uint32_t)a16(L.sg + 4 * C.nw);
+  L.tb = L.sg + 4 * C.nw;
+  L.smem_free = (uint32_t)a16(L.tb + 4 * C.nw);
   size_t o = 0;
   L.cv = (uint32_t)o;
   o = a16(o + b * C.E);
@@ -73,6 +74,7 @@ template <class T>
 struct ShotView {
   TeamCtl *ctl;
   uint32_t *e, *s, *s0, *sg;
+  uint32_t *tb;  // qubits targeted by a candidate move of the current tick
   T *CV, *VC0, *VC1;
   volatile uint8_t *cstate;
   uint32_t *cprio;
@@ -88,6 +90,7 @@ __device__ __forceinline__ ShotView<T> make_view(const Layout &Ly, uint8_t *base
   V.s = reinterpret_cast<uint32_t *>(base + Ly.s);
   V.s0 = reinterpret_cast<uint32_t *>(base + Ly.s0);
   V.sg = reinterpret_cast<uint32_t *>(base + Ly.sg);
+  V.tb = reinterpret_cast<uint32_t *>(base + Ly.tb);
   V.CV = reinterpret_cast<T *>(msg + Ly.cv);
   V.VC0 = reinterpret_cast<T *>(msg + Ly.vc0);
   V.VC1 = reinterpret_cast<T *>(msg + Ly.vc1);
@@ -151,6 +154,7 @@ __device__ void shot_init(const Team &tm, const LaunchArgs &A, const DevPoint &p
     }
     V.e[w] = word;
     V.sg[w] = 0;
+    V.tb[w] = 0;
   }
   for (int i = tm.rank(); i < C.E; i += tm.size()) {
     V.CV[i] = T(0);
@@ -164,6 +168,8 @@ __device__ void shot_init(const Team &tm, const LaunchArgs &A, const DevPoint &p
     V.ctl->err = 0;
     V.ctl->logmask = 0;
     V.ctl->done = 0;
+    V.ctl->work[0] = 0;
+    V.ctl->work[1] = 0;
   }
   tm.sync();
   for (int w = tm.rank(); w < C.mw; w += tm.size()) {
@@ -218,9 +224,22 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
   const FlipCtx F{V.e, V.s, V.sg, &ctl->defects, &ctl->moves};
   const bool frame_s0 = (FB == LIM_FB_BIT_DISCRETE) || P.gauge_on_move;
   const uint32_t *seff = frame_s0 ? V.s0 : V.s;  // effective syndrome of the check half-sweep
+  // Overlap (fused mode without gauge switches): the check half-sweep of this
+  // tick's first sweep reads the messages of two sweeps back and writes the third
+  // buffer, so it does not depend on the feedback except through the sign
+  // (-1)^{s_c} of Eq. 2.  It runs together with the feedback scan under the
+  // syndrome before the feedback, and afterwards the rows of the checks whose
+  // syndrome bit the moves toggled are negated (exact in every storage format:
+  // rounding and saturation are symmetric).  sigma is identically zero here, so
+  // its words hold the syndrome that the signs of the newest messages refer to.
+  const bool overlap = fused && !P.gauge_on_move;
+  uint32_t *const s_sign = V.sg;
   R.ticks = t;
-  // the sweep's chunk counter; published by the barrier after the feedback scan
-  if (!Team::is_warp && tm.rank() == 0) ctl->work = 0;
+  // chunk counters of the sweep alternate by tick: the one of the next tick was
+  // last used before the previous tick's final barrier
+  int32_t *const work = Team::is_warp ? nullptr : &ctl->work[t & 1];
+  if (!Team::is_warp && tm.rank() == 0) ctl->work[(t + 1) & 1] = 0;
+  int nc = 0;
   // --- read-out + feedback (+ the qubit half-sweep of sweep 1, which reads the
   //     same messages and does not depend on the feedback) --------------------
   if (FB == LIM_FB_CHECK_MOVE) {
@@ -269,9 +288,24 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
         V.cprio[c] = u.y;
         V.ctgt[c] = vstar;
         V.cstate[c] = kPending;
+        atomicOr(V.tb + (vstar >> 5), 1u << (vstar & 31));
       }
     }
     if (t < pt.T && !fused) var_pass<PREC, false>(tm.rank(), tm.size(), C, P, CV, VCc, VCn, F);
+    if (overlap) {
+      if (t == 1)
+        for (int w = tm.rank(); w < C.mw; w += tm.size()) s_sign[w] = V.s[w];
+      // The very first sweep maps m = 0 to CV = 0 (every check has degree >= 2),
+      // which the zeroed second buffer already holds.
+      if (t < pt.T && R.sweeps > 0) {
+        if (pt.msg_smem)
+          fused_pass<PREC, RULE, true>(tm.rank(), tm.size(), C, P, SBitWords{V.s},
+                                       B[(R.vc_sel + 2) % 3], B[(R.vc_sel + 1) % 3], work);
+        else
+          fused_pass<PREC, RULE, false>(tm.rank(), tm.size(), C, P, SBitWords{V.s},
+                                        B[(R.vc_sel + 2) % 3], B[(R.vc_sel + 1) % 3], work);
+      }
+    }
   } else {
     // Bit-centric rule, Eq. 3-4: f_v = 1[L_v > 0]; the gauge switch of Sec. S2
     // is a toggle of sigma_v (the stored messages stay as they are).
@@ -280,7 +314,7 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
   tm.sync();
   clk.mark(1);
   if (FB == LIM_FB_CHECK_MOVE) {
-    const int nc = ctl->ncand;
+    nc = ctl->ncand;
     if (nc > 0) {
       if (!P.gauge_on_move) {
         // Sequential semantics of the rings in priority order, resolved in
@@ -294,11 +328,16 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
             const int c = V.clist[j];
             if (V.cstate[c] != kPending) continue;
             const uint32_t pc = V.cprio[c];
-            const int cb = __ldg(C.c_ptr + c), ce = __ldg(C.c_ptr + c + 1);
+            const int cb = C.dc_u ? c * C.dc_u : __ldg(C.c_ptr + c);
+            const int ce = C.dc_u ? cb + C.dc_u : __ldg(C.c_ptr + c + 1);
             int ready = 1, active = 1;
             for (int jj = cb; jj < ce && ready; jj++) {
               const int u = __ldg(C.c_var + jj);
-              for (int q = __ldg(C.v_ptr + u); q < __ldg(C.v_ptr + u + 1); q++) {
+              // only a qubit that some candidate targets can change N(c)
+              if (!((V.tb[u >> 5] >> (u & 31)) & 1)) continue;
+              const int qb = C.dv_u ? u * C.dv_u : __ldg(C.v_ptr + u);
+              const int qe = C.dv_u ? qb + C.dv_u : __ldg(C.v_ptr + u + 1);
+              for (int q = qb; q < qe; q++) {
                 const int c2 = __ldg(C.v_chk + q);
                 if (c2 == c) continue;
                 const uint8_t st2 = V.cstate[c2];
@@ -321,8 +360,10 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
         }
         for (int j = tm.rank(); j < nc; j += tm.size()) {
           const int c = V.clist[j];
-          if (V.cstate[c] == kExec) flip_bits(C, F, V.ctgt[c]);
+          const int v = V.ctgt[c];
+          if (V.cstate[c] == kExec) flip_bits(C, F, v);
           V.cstate[c] = kNone;
+          atomicAnd(V.tb + (v >> 5), ~(1u << (v & 31)));
         }
       } else if (tm.rank() == 0) {
         // With the gauge switch on every move, a flip changes later beliefs:
@@ -383,10 +424,31 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
   if (t == pt.T) return true;
   // --- check half-sweep of sweep 1, then sweeps 2..K ---------------------------
   if (fused) {
-    int32_t *work = Team::is_warp ? nullptr : &ctl->work;
-    for (int k = 0; k < P.K; k++) {
+    int k0 = 0;
+    if (overlap) {
+      if (nc > 0) {  // sign fix of the rows whose check the moves toggled
+        T *const out = B[(R.vc_sel + 1) % 3];
+        for (int w = tm.rank(); w < C.mw; w += tm.size()) {
+          uint32_t d = V.s[w] ^ s_sign[w];
+          if (!d) continue;
+          s_sign[w] = V.s[w];
+          if (R.sweeps == 0) continue;  // the first sweep's messages are all zero
+          while (d) {
+            const int c = 32 * w + __ffs(d) - 1;
+            d &= d - 1;
+            negate_row<PREC>(out + (size_t)c * C.dc_u, C.dc_u);
+          }
+        }
+        tm.sync();
+      }
+      clk.mark(3);
+      R.vc_sel = (R.vc_sel + 1) % 3;
+      R.sweeps++;
+      k0 = 1;
+    }
+    for (int k = k0; k < P.K; k++) {
       if (k > 0 && work) {  // reset the chunk counter between sweeps
-        if (tm.rank() == 0) ctl->work = 0;
+        if (tm.rank() == 0) *work = 0;
         tm.sync();
       }
       // The very first sweep maps m = 0 to CV = 0 (every check has degree >= 2),

@@ -213,7 +213,8 @@ struct FlipCtx {
 
 __device__ __forceinline__ void flip_bits(const DevCode &C, const FlipCtx &F, int v) {
   atomicXor(F.e + (v >> 5), 1u << (v & 31));
-  const int b = __ldg(C.v_ptr + v), en = __ldg(C.v_ptr + v + 1);
+  const int b = C.dv_u ? v * C.dv_u : __ldg(C.v_ptr + v);
+  const int en = C.dv_u ? b + C.dv_u : __ldg(C.v_ptr + v + 1);
   int delta = 0;
   for (int t = b; t < en; t++) {
     const int c = __ldg(C.v_chk + t);
@@ -630,7 +631,7 @@ __device__ __noinline__ void fused_run(int rank, int size, const DevCode &C, con
   }
   constexpr int NP = DC * (DV - 1);
   constexpr int NB = SMEM ? 2 : (NP <= 4 ? 4 : (NP <= 6 ? 2 : 1));
-  if (work && !SMEM) fused_loop_dyn<PREC, RULE, DC, DV, NB>(work, C, P, sbit, CVp, CVn);
+  if (work && (!SMEM || C.m >= 4 * size)) fused_loop_dyn<PREC, RULE, DC, DV, NB>(work, C, P, sbit, CVp, CVn);
   else fused_loop<PREC, RULE, DC, DV, NB>(rank, size, C, P, sbit, CVp, CVn);
 }
 
@@ -643,6 +644,18 @@ __device__ __forceinline__ void fused_pass(int rank, int size, const DevCode &C,
   else if (C.dc_u == 4 && C.dv_u == 4) fused_run<PREC, RULE, SMEM, 4, 4>(rank, size, C, P, sbit, CVp, CVn, work);
   else if (C.dc_u == 6 && C.dv_u == 3) fused_run<PREC, RULE, SMEM, 6, 3>(rank, size, C, P, sbit, CVp, CVn, work);
   else fused_run<PREC, RULE, SMEM, 2, 2>(rank, size, C, P, sbit, CVp, CVn, work);
+}
+
+// Negate a row of n stored messages; a zero stays +0 (the stored form of a zero
+// magnitude).
+template <int PREC>
+__device__ __forceinline__ void negate_row(typename MT<PREC>::T *row, int n) {
+  using M = MT<PREC>;
+  using A = typename M::A;
+  for (int j = 0; j < n; j++) {
+    const A x = M::ld(row + j);
+    M::st(row + j, x == A(0) ? A(0) : -x);
+  }
 }
 
 struct SBitWords {  // s~ from bit-packed words

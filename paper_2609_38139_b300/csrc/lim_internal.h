@@ -86,7 +86,7 @@ struct LaunchArgs {
 
 // Per-code sizes used to lay out team memory.
 struct CodeLayout {
-  size_t bits_bytes;   // control block + e, s, s0, sigma bit vectors (always shared memory)
+  size_t bits_bytes;   // control block + e, s, s0, sigma, move-target bit vectors (shared memory)
   size_t msg_bytes;    // CV, VC (two buffers)
   size_t chk_bytes;    // per-check feedback scratch
 };

@@ -117,7 +117,7 @@ size_t msg_bytes(int prec) { return msg_bytes_dev(prec); }
 CodeLayout code_layout(const DevCode &c, int prec) {
   CodeLayout L;
   const size_t b = msg_bytes_dev(prec);
-  L.bits_bytes = a16(sizeof(TeamCtl) + 4 * (size_t)(2 * c.nw + 2 * c.mw));
+  L.bits_bytes = a16(sizeof(TeamCtl) + 4 * (size_t)(3 * c.nw + 2 * c.mw));
   L.msg_bytes = a16(b * c.E) * 3;
   L.chk_bytes = a16(c.m) + 3 * a16(4 * (size_t)c.m);
   return L;
