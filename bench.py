@@ -222,7 +222,8 @@ def main():
     ap.add_argument("--workload", default="toric2d_sweep")
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--variant", default="auto")
-    ap.add_argument("--shots", type=int, default=32, help="shots per point per step")
+    ap.add_argument("--shots", type=int, default=0,
+                    help="shots per point per step (default: the workload's bench_shots, else 32)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -257,6 +258,8 @@ def main():
     ctx = L.Context(local)
     sizes = [x for x in args.sizes.split(",") if x]
     ps = [x for x in args.ps.split(",") if x]
+    if args.shots <= 0:
+        args.shots = I.WORKLOADS[args.workload].get("bench_shots", 32)
     w, pts = workload(args.workload, args.shots, sizes, ps)
     if args.rule:
         w = dict(w, rule=args.rule)
@@ -370,32 +373,47 @@ def main():
     if args.phases and phase.sum() > 0:
         line["phase_share"] = {n: round(float(v / phase.sum()), 4) for n, v in zip(L.PHASES, phase)}
         line["phase_cycles_per_tick"] = float(phase.sum() / max(1, ticks))
-    # end to end through the public API: run + read records and tallies back
+    # end to end through the public API: lim_run_batch_host, one blocking call per
+    # step with host buffers -- the step's initial errors are copied in from
+    # page-locked host memory, the records, final residuals and tallies are
+    # copied back.  The errors are the library's own samples for those shot ids
+    # (lim_sample_noise, drawn before the timed region), so the work per step is
+    # the same as in the device-timed steps.
     if not args.no_e2e:
-        # the batch captured once as a CUDA graph (lim_graph_create) and replayed
-        # with a fresh shot window per step; records and tallies read back
-        rec_host = torch.empty(batch.rec.numel(), dtype=torch.uint8, pin_memory=True)
-        tal_host = torch.empty(batch.tally.numel(), dtype=torch.uint8, pin_memory=True)
-        batch.points = step_points(0)
-        batch.pts = L._points(batch.points)
-        batch.capture()
+        hb = L.HostBatch(ctx, [pt[:3] + (0,) + tuple(pt[4:]) for pt in step_points(0)], prm)
+        e2e_steps = []
+        for i in range(args.steps):
+            off = ((step_id[0] + i) * world + rank) * args.shots
+            buf = torch.zeros(hb.nshots * hb.words, dtype=torch.int32, pin_memory=True)
+            view = buf.view(hb.nshots, hb.words)
+            row = 0
+            for pt in hb.points:
+                c, p, n, s0, pid = pt[:5]
+                e, _ = L.sample_noise(c, p, 0, pid, s0 + off, n)
+                view[row:row + n, :e.shape[1]].copy_(e.cpu())
+                row += n
+            e2e_steps.append((off, buf))
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
         e_ticks = 0
-        for i in range(args.steps):
-            batch.replay(0, (step_id[0] * world) * args.shots, stream)
-            step_id[0] += 1
-            rec_host.copy_(batch.rec, non_blocking=True)
-            tal_host.copy_(batch.tally, non_blocking=True)
-            torch.cuda.synchronize()
-            arr = np.frombuffer(tal_host.numpy().tobytes(), dtype=L.TALLY_DTYPE)
-            e_ticks += int(arr["ticks"].sum())
+        for off, buf in e2e_steps:
+            hb.set_shot_offset(off)
+            hb.run(0, e0=buf, stream=stream)
+            e_ticks += int(hb.tallies()["ticks"].sum())
         e_dt = time.perf_counter() - t0
+        step_id[0] += args.steps
+        if world > 1:
+            tt = torch.tensor([e_dt], dtype=torch.float64, device=torch.device("cuda", local))
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_dt = float(tt.item())
         line["e2e"] = {"value": e_ticks / e_dt * world, "unit": "shot-ticks/s",
-                       "h2d_bytes_per_step": 0,
-                       "d2h_bytes_per_step": int(batch.rec.numel() + batch.tally.numel()),
-                       "note": "graph replay per step (lim_graph_launch); noise is sampled on the "
-                               "device (part of the method); records and tallies are read back"}
+                       "h2d_bytes_per_step": hb.h2d_bytes(),
+                       "d2h_bytes_per_step": hb.d2h_bytes(),
+                       "note": "lim_run_batch_host per step: initial errors of the step's shots "
+                               "copied in from page-locked host memory, records, final residuals "
+                               "and tallies copied back, inside the timed region"}
         line["gpu_launches"] = args.steps
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.precision, args.cpu_seconds,

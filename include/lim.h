@@ -234,6 +234,34 @@ int lim_run_batch(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_p
                   uint64_t seed, void *workspace, size_t workspace_bytes, lim_shot_record *rec,
                   uint32_t *e_final, lim_tally *tally, void *stream);
 
+/* lim_run_batch from given initial errors instead of sampled noise (the
+ * decoding problem of the Preliminaries: the error, hence the syndrome s = H_X e,
+ * comes from outside; the decoder returns the residual and the failure flag).
+ *   e0  device, one row of max_n_words words per shot (lim_final_words; same
+ *       order and stride as e_final), bit v % 32 of word v / 32 = e_v; bits
+ *       beyond a code's n are ignored.  The points' p is not used; the clock
+ *       rings still draw from (seed, point, shot).  Read by the kernel while it
+ *       runs: keep it unchanged until the stream passes the launch.
+ * Feeding back the errors lim_sample_noise draws for (seed, point, shot) gives
+ * exactly the results of lim_run_batch.  Variant PLAIN is refused. */
+int lim_run_batch_from(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+                       uint64_t seed, const uint32_t *e0, void *workspace, size_t workspace_bytes,
+                       lim_shot_record *rec, uint32_t *e_final, lim_tally *tally, void *stream);
+
+/* Host-buffer form of lim_run_batch_from, one blocking call: copies e0_host
+ * (nullable: then the noise is sampled on the device as in lim_run_batch) into a
+ * staging area of the workspace, runs the batch, copies rec, e_final and tally
+ * back into the host buffers (rec_host and e_final_host nullable; shapes as in
+ * lim_run_batch) and waits for the stream.  Host buffers in page-locked memory
+ * make the copies asynchronous.  workspace (device) >= lim_workspace_size_host()
+ * bytes.  Variant PLAIN is refused. */
+int lim_workspace_size_host(lim_ctx *ctx, const lim_point *pts, uint32_t npts,
+                            const lim_params *prm, size_t *bytes);
+int lim_run_batch_host(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+                       uint64_t seed, const uint32_t *e0_host, void *workspace,
+                       size_t workspace_bytes, lim_shot_record *rec_host, uint32_t *e_final_host,
+                       lim_tally *tally_host, void *stream);
+
 /* lim_run_batch without any device allocation, for callers that cannot call
  * cudaMalloc while they run (a real-time loop that must not block on the
  * allocator, memory owned by another framework's pool, launches being recorded
@@ -261,6 +289,12 @@ typedef struct lim_graph lim_graph;
 int lim_graph_create(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
                      void *workspace, size_t workspace_bytes, lim_shot_record *rec,
                      uint32_t *e_final, lim_tally *tally, lim_graph **out);
+/* The same over given initial errors (lim_run_batch_from): every launch reads
+ * e0, whose contents the caller may change between launches. */
+int lim_graph_create_from(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+                          const uint32_t *e0, void *workspace, size_t workspace_bytes,
+                          lim_shot_record *rec, uint32_t *e_final, lim_tally *tally,
+                          lim_graph **out);
 int lim_graph_launch(lim_graph *graph, uint64_t seed, uint32_t shot_offset, void *stream);
 int lim_graph_destroy(lim_graph *graph);
 

@@ -578,35 +578,141 @@ int lim_final_words(const lim_point *pts, uint32_t npts, int32_t *words) {
   return LIM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// lim_run_batch with optional caller-given initial errors (e0, device).
+int run_batch(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+              uint64_t seed, const uint32_t *e0, void *workspace, size_t workspace_bytes,
+              lim_shot_record *rec, uint32_t *e_final, lim_tally *tally, void *stream) {
+  if (!tally || !workspace) return bad(LIM_E_INVAL, "null tally or workspace");
+  DevParams dp;
+  int st = derive(prm, dp);
+  if (st) return st;
+  Plan pl;
+  st = make_plan(ctx, pts, npts, prm, dp, pl);
+  if (st) return st;
+  if (workspace_bytes < pl.workspace) return bad(LIM_E_NOMEM, "workspace too small");
+  if (pl.plain) {
+    if (e0) return bad(LIM_E_UNSUPPORTED, "the plain path samples its own noise");
+    cudaError_t err = cudaMemsetAsync(tally, 0, sizeof(lim_tally) * npts, (cudaStream_t)stream);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync");
+    return run_plain(ctx, pl, pts, npts, prm, dp, seed, workspace, rec, e_final, tally, stream);
+  }
+  LaunchArgs a;
+  fill_args(pl, pts, npts, prm, dp, seed, workspace, a);
+  a.rec = rec;
+  a.e_final = e_final;
+  if (e_final) lim_final_words(pts, npts, &a.e_final_words);
+  a.e_init = e0;
+  if (e0) lim_final_words(pts, npts, &a.e_init_words);
+  a.tally = tally;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t err = cudaMemsetAsync(workspace, 0, 256, s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(tally, 0, sizeof(lim_tally) * npts, s);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync");
+  if (a.total_items == 0) return LIM_OK;
+  return launch_batch(a, pl.warp, pl.grid, pl.block, pl.smem, stream);
+}
+
+// Staging areas of lim_run_batch_host inside the workspace, after the batch's own.
+struct HostStaging {
+  size_t e0, rec, fin, tally, total;
+};
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int host_staging(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+                 HostStaging &hs) {
+  size_t ws = 0;
+  int st = lim_workspace_size(ctx, pts, npts, prm, &ws);
+  if (st) return st;
+  int32_t words = 0;
+  st = lim_final_words(pts, npts, &words);
+  if (st) return st;
+  uint64_t items = 0;
+  for (uint32_t i = 0; i < npts; i++) items += pts[i].shots;
+  hs.e0 = a256(ws);
+  hs.rec = hs.e0 + a256(items * (size_t)words * 4);
+  hs.fin = hs.rec + a256(items * sizeof(lim_shot_record));
+  hs.tally = hs.fin + a256(items * (size_t)words * 4);
+  hs.total = hs.tally + a256(npts * sizeof(lim_tally));
+  return LIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int lim_run_batch(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
                   uint64_t seed, void *workspace, size_t workspace_bytes, lim_shot_record *rec,
                   uint32_t *e_final, lim_tally *tally, void *stream) {
   return guarded([&] {
-    if (!tally || !workspace) return bad(LIM_E_INVAL, "null tally or workspace");
-    DevParams dp;
-    int st = derive(prm, dp);
+    return run_batch(ctx, pts, npts, prm, seed, nullptr, workspace, workspace_bytes, rec, e_final,
+                     tally, stream);
+  });
+}
+
+int lim_run_batch_from(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+                       uint64_t seed, const uint32_t *e0, void *workspace, size_t workspace_bytes,
+                       lim_shot_record *rec, uint32_t *e_final, lim_tally *tally, void *stream) {
+  return guarded([&] {
+    if (!e0) return bad(LIM_E_INVAL, "null e0");
+    return run_batch(ctx, pts, npts, prm, seed, e0, workspace, workspace_bytes, rec, e_final, tally,
+                     stream);
+  });
+}
+
+int lim_workspace_size_host(lim_ctx *ctx, const lim_point *pts, uint32_t npts,
+                            const lim_params *prm, size_t *bytes) {
+  return guarded([&] {
+    if (!bytes) return bad(LIM_E_INVAL, "null output");
+    HostStaging hs;
+    int st = host_staging(ctx, pts, npts, prm, hs);
     if (st) return st;
-    Plan pl;
-    st = make_plan(ctx, pts, npts, prm, dp, pl);
+    *bytes = hs.total;
+    return LIM_OK;
+  });
+}
+
+int lim_run_batch_host(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+                       uint64_t seed, const uint32_t *e0_host, void *workspace,
+                       size_t workspace_bytes, lim_shot_record *rec_host, uint32_t *e_final_host,
+                       lim_tally *tally_host, void *stream) {
+  return guarded([&] {
+    if (!tally_host || !workspace) return bad(LIM_E_INVAL, "null tally or workspace");
+    if (prm && prm->variant == LIM_VARIANT_PLAIN)
+      return bad(LIM_E_UNSUPPORTED, "lim_run_batch_host runs the persistent kernel only");
+    HostStaging hs;
+    int st = host_staging(ctx, pts, npts, prm, hs);
     if (st) return st;
-    if (workspace_bytes < pl.workspace) return bad(LIM_E_NOMEM, "workspace too small");
-    if (pl.plain) {
-      cudaError_t err = cudaMemsetAsync(tally, 0, sizeof(lim_tally) * npts, (cudaStream_t)stream);
-      if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync");
-      return run_plain(ctx, pl, pts, npts, prm, dp, seed, workspace, rec, e_final, tally, stream);
-    }
-    LaunchArgs a;
-    fill_args(pl, pts, npts, prm, dp, seed, workspace, a);
-    a.rec = rec;
-    a.e_final = e_final;
-    if (e_final) lim_final_words(pts, npts, &a.e_final_words);
-    a.tally = tally;
+    if (workspace_bytes < hs.total) return bad(LIM_E_NOMEM, "workspace too small");
+    int32_t words = 0;
+    lim_final_words(pts, npts, &words);
+    uint64_t items = 0;
+    for (uint32_t i = 0; i < npts; i++) items += pts[i].shots;
+    uint8_t *w = static_cast<uint8_t *>(workspace);
+    uint32_t *e0_dev = reinterpret_cast<uint32_t *>(w + hs.e0);
+    lim_shot_record *rec_dev = reinterpret_cast<lim_shot_record *>(w + hs.rec);
+    uint32_t *fin_dev = reinterpret_cast<uint32_t *>(w + hs.fin);
+    lim_tally *tally_dev = reinterpret_cast<lim_tally *>(w + hs.tally);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t err = cudaMemsetAsync(workspace, 0, 256, s);
-    if (err == cudaSuccess) err = cudaMemsetAsync(tally, 0, sizeof(lim_tally) * npts, s);
-    if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync");
-    if (a.total_items == 0) return LIM_OK;
-    return launch_batch(a, pl.warp, pl.grid, pl.block, pl.smem, stream);
+    const size_t e_bytes = items * (size_t)words * 4;
+    cudaError_t err = cudaSuccess;
+    if (e0_host && e_bytes) err = cudaMemcpyAsync(e0_dev, e0_host, e_bytes, cudaMemcpyHostToDevice, s);
+    if (err != cudaSuccess) return cuda_fail(err, "copy of e0 to the device");
+    st = run_batch(ctx, pts, npts, prm, seed, e0_host ? e0_dev : nullptr, workspace, hs.e0,
+                   rec_host ? rec_dev : nullptr, e_final_host ? fin_dev : nullptr, tally_dev, stream);
+    if (st) return st;
+    if (rec_host && items)
+      err = cudaMemcpyAsync(rec_host, rec_dev, items * sizeof(lim_shot_record), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess && e_final_host && e_bytes)
+      err = cudaMemcpyAsync(e_final_host, fin_dev, e_bytes, cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(tally_host, tally_dev, npts * sizeof(lim_tally), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    return err == cudaSuccess ? LIM_OK : cuda_fail(err, "copy of the results to the host");
   });
 }
 
@@ -628,6 +734,14 @@ extern "C" {
 int lim_graph_create(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
                      void *workspace, size_t workspace_bytes, lim_shot_record *rec,
                      uint32_t *e_final, lim_tally *tally, lim_graph **out) {
+  return lim_graph_create_from(ctx, pts, npts, prm, nullptr, workspace, workspace_bytes, rec, e_final,
+                               tally, out);
+}
+
+int lim_graph_create_from(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+                          const uint32_t *e0, void *workspace, size_t workspace_bytes,
+                          lim_shot_record *rec, uint32_t *e_final, lim_tally *tally,
+                          lim_graph **out) {
   return guarded([&] {
     if (!out || !tally || !workspace) return bad(LIM_E_INVAL, "null argument");
     DevParams dp;
@@ -645,6 +759,8 @@ int lim_graph_create(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const li
     g->args.rec = rec;
     g->args.e_final = e_final;
     if (e_final) lim_final_words(pts, npts, &g->args.e_final_words);
+    g->args.e_init = e0;
+    if (e0) lim_final_words(pts, npts, &g->args.e_init_words);
     g->args.tally = tally;
     for (uint32_t i = 0; i < npts; i++) g->shot0.push_back(pts[i].shot0);
     cudaError_t err = cudaGraphCreate(&g->graph, 0);

@@ -134,13 +134,25 @@ __device__ __forceinline__ void write_trace(const Team &tm, const LaunchArgs &A,
 }
 
 // --- init: noise and initial syndrome (Preliminaries), m = 0 (Algorithm 1) ----
+// The initial error is the sampled i.i.d. noise, or row `item` of A.e_init when
+// the caller gives the errors (bits beyond n ignored).
 template <class Team, int PREC>
 __device__ void shot_init(const Team &tm, const LaunchArgs &A, const DevPoint &pt, const DevCode &C,
-                          uint32_t shot, const ShotView<typename MT<PREC>::T> &V, ShotRegs &R) {
+                          uint32_t shot, uint64_t item, const ShotView<typename MT<PREC>::T> &V,
+                          ShotRegs &R) {
   using T = typename MT<PREC>::T;
   const DevParams &P = A.prm;
   for (int w = tm.rank(); w < C.nw; w += tm.size()) {
     uint32_t word = 0;
+    if (A.e_init) {
+      word = A.e_init[item * (uint64_t)A.e_init_words + w];
+      const int rem = C.n - 32 * w;
+      if (rem < 32) word &= (1u << rem) - 1u;
+      V.e[w] = word;
+      V.sg[w] = 0;
+      V.tb[w] = 0;
+      continue;
+    }
 #pragma unroll 1
     for (int j = 0; j < 8; j++) {
       const int v0 = 32 * w + 4 * j;
@@ -576,7 +588,7 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ Lau
     const ShotView<T> V = make_view<T>(Ly, tsm, msg, chk);
     ShotRegs R;
     PhaseClock clk{clock64(), (A.prm.profile && tm.rank() == 0) ? A.tally[pidx].phase_cycles : nullptr};
-    shot_init<Team, PREC>(tm, A, pt, C, shot, V, R);
+    shot_init<Team, PREC>(tm, A, pt, C, shot, item, V, R);
     clk.mark(0);
     if (!R.converged)
       for (int t = 1; t <= pt.T; t++)
@@ -616,7 +628,7 @@ __global__ void __launch_bounds__(1024) plain_init_kernel(const __grid_constant_
   const DevCode &C = A.codes[pt.code];
   const auto V = plain_view<PREC>(A, C);
   ShotRegs R;
-  shot_init<TeamCTA, PREC>(tm, A, pt, C, pt.shot0 + blockIdx.x, V, R);
+  shot_init<TeamCTA, PREC>(tm, A, pt, C, pt.shot0 + blockIdx.x, 0, V, R);
   if (tm.rank() == 0) {
     store_regs(V.ctl, R);
     V.ctl->done = R.converged;

@@ -76,6 +76,8 @@ struct LaunchArgs {
   lim_shot_record *rec;    // nullable
   uint32_t *e_final;       // nullable
   int32_t e_final_words;
+  const uint32_t *e_init;  // nullable: initial errors given per item instead of sampled noise
+  int32_t e_init_words;    // row stride of e_init (words per item)
   lim_tally *tally;        // [npts]
   // trace of one item (lim_trace)
   uint32_t *trace_e, *trace_s;

@@ -393,13 +393,15 @@ def p_grid(lo: float, hi: float, npts: int) -> List[float]:
     return [float(x) for x in np.linspace(lo, hi, npts)]
 
 
+# ``bench_shots``: shots per point in one benchmark step (default 32), enough to
+# keep every team of the GPU busy through the uneven termination of the shots.
 WORKLOADS = {
     # 2D toric code L=8, p=0.05, 1000 shots, tick budget 4L; min-sum FP32.
-    "toric2d_L8_small": dict(family="toric2d", sizes=[8], p=[0.05], shots=1000,
+    "toric2d_L8_small": dict(family="toric2d", sizes=[8], p=[0.05], shots=1000, bench_shots=1000,
                              q=0.05, clamp=1000.0, tau=0.1, dt_tick=0.1, K=1,
                              budget="4L"),
     # open repetition chain d=2000, p=0.45, discrete (bit-centric) machine.
-    "rep2000_p045": dict(family="rep", sizes=[2000], p=[0.45], shots=1000,
+    "rep2000_p045": dict(family="rep", sizes=[2000], p=[0.45], shots=1000, bench_shots=1000,
                          q=0.05, clamp=1000.0, tau=0.1, dt_tick=0.1, K=1, budget="4d+1",
                          feedback="bit_discrete"),
     # batched 2D toric sweep, L in {16,32,64,128}, 11 p points in 0.02-0.12.
@@ -409,15 +411,17 @@ WORKLOADS = {
     # 3D toric point-like sector, 16-bit messages.
     "toric3d_point_sweep": dict(family="toric3d_point", sizes=[8, 12, 16, 24],
                                 p=p_grid(0.01, 0.05, 9), shots=100000, q=0.05,
-                                clamp=1000.0, tau=0.1, dt_tick=0.1, K=1, budget="40L"),
+                                clamp=1000.0, tau=0.1, dt_tick=0.1, K=1, budget="40L",
+                                bench_shots=64),
     # 3D toric membrane-like sector, int16 quantised min-sum.
     "toric3d_membrane_sweep": dict(family="toric3d_membrane", sizes=[6, 8, 12, 16],
                                    p=p_grid(0.01, 0.06, 9), shots=100000, q=0.125,
-                                   clamp=1000.0, tau=0.1, dt_tick=0.1, K=1, budget=10000),
+                                   clamp=1000.0, tau=0.1, dt_tick=0.1, K=1, budget=10000,
+                                   bench_shots=512),
     # bivariate-bicycle codes, int8 quantised min-sum, 1e6 shots mixed over 27 points.
     "bb_mixed": dict(family="bb", sizes=[(6, 6), (15, 3), (12, 6)], p=p_grid(0.01, 0.08, 9),
                      shots=1000000 // 27, q=0.05, clamp=1000.0, tau=0.1, dt_tick=0.1, K=1,
-                     budget=10000),
+                     budget=10000, bench_shots=1024),
     # Table S1 discretisations (fine dt, relaxation alpha = dt/tau, budget t_max/dt) with the
     # paper's check rule (sum-product, Eq. 2) at the smaller sizes of each family; t_max = 1000
     # also for the families the table leaves open.

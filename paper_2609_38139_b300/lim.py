@@ -34,7 +34,8 @@ MAX_POINTS = 128
 EXPORTS = ["lim_last_error", "lim_version", "lim_ctx_create", "lim_ctx_destroy", "lim_code_from_csr",
            "lim_code_rep", "lim_code_toric2d", "lim_code_toric3d", "lim_code_bb", "lim_code_info",
            "lim_code_export", "lim_code_destroy", "lim_sample_noise", "lim_params_check",
-           "lim_workspace_size", "lim_run_batch", "lim_run_batch_static", "lim_graph_create",
+           "lim_workspace_size", "lim_run_batch", "lim_run_batch_from", "lim_workspace_size_host",
+           "lim_run_batch_host", "lim_run_batch_static", "lim_graph_create", "lim_graph_create_from",
            "lim_graph_launch", "lim_graph_destroy", "lim_autotune", "lim_final_words",
            "lim_trace", "lim_bp_sweeps", "lim_readout"]
 
@@ -103,6 +104,14 @@ def lib() -> ctypes.CDLL:
     L.lim_workspace_size.argtypes = [vp, vp, u32, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]
     L.lim_run_batch.argtypes = [vp, vp, u32, ctypes.POINTER(Params), u64, vp, ctypes.c_size_t, vp, vp,
                                 vp, vp]
+    L.lim_run_batch_from.argtypes = [vp, vp, u32, ctypes.POINTER(Params), u64, vp, vp, ctypes.c_size_t,
+                                     vp, vp, vp, vp]
+    L.lim_workspace_size_host.argtypes = [vp, vp, u32, ctypes.POINTER(Params),
+                                          ctypes.POINTER(ctypes.c_size_t)]
+    L.lim_run_batch_host.argtypes = [vp, vp, u32, ctypes.POINTER(Params), u64, vp, vp, ctypes.c_size_t,
+                                     vp, vp, vp, vp]
+    L.lim_graph_create_from.argtypes = [vp, vp, u32, ctypes.POINTER(Params), vp, vp, ctypes.c_size_t,
+                                        vp, vp, vp, pp]
     L.lim_run_batch_static.argtypes = [vp, vp, u32, ctypes.POINTER(Params), u64, vp, vp, vp, vp]
     L.lim_graph_create.argtypes = [vp, vp, u32, ctypes.POINTER(Params), vp, ctypes.c_size_t, vp, vp,
                                    vp, pp]
@@ -272,6 +281,70 @@ def final_words(points) -> int:
     return int(w.value)
 
 
+def workspace_size_host(ctx: Context, points, prm: Params) -> int:
+    pts = _points(points)
+    out = ctypes.c_size_t()
+    check(lib().lim_workspace_size_host(ctx.handle, pts, len(points), ctypes.byref(prm),
+                                        ctypes.byref(out)), "lim_workspace_size_host")
+    return int(out.value)
+
+
+class HostBatch:
+    """``lim_run_batch_host``: one blocking call with host buffers -- the
+    initial errors go in (or None: noise sampled on the device), the records,
+    final residuals and tallies come out.  Page-locked host buffers are kept
+    here and reused across calls."""
+
+    def __init__(self, ctx: Context, points, prm: Params):
+        import torch
+        self.ctx, self.points, self.prm = ctx, list(points), prm
+        self.pts = _points(self.points)
+        self.nshots = sum(int(p[2]) for p in self.points)
+        self.words = final_words(self.points)
+        self.ws_bytes = workspace_size_host(ctx, self.points, prm)
+        self.ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8,
+                              device=torch.device("cuda", ctx.device))
+        self.e0 = torch.zeros(max(self.nshots * self.words, 1), dtype=torch.int32, pin_memory=True)
+        self.rec = torch.empty(max(self.nshots, 1) * RECORD_DTYPE.itemsize, dtype=torch.uint8,
+                               pin_memory=True)
+        self.e_final = torch.empty(max(self.nshots * self.words, 1), dtype=torch.int32, pin_memory=True)
+        self.tally = torch.empty(len(self.points) * TALLY_DTYPE.itemsize, dtype=torch.uint8,
+                                 pin_memory=True)
+
+    def set_shot_offset(self, offset: int) -> None:
+        """Shots shot0 + offset ... of every point in the next run."""
+        for i, pt in enumerate(self.points):
+            self.pts[i].shot0 = int(pt[3]) + int(offset)
+
+    def run(self, seed: int, with_e0: bool = True, stream=None, e0=None) -> None:
+        """One blocking call; ``e0`` (a page-locked host tensor) replaces the
+        batch's own e0 buffer."""
+        src = e0 if e0 is not None else self.e0
+        check(lib().lim_run_batch_host(self.ctx.handle, self.pts, len(self.points),
+                                       ctypes.byref(self.prm), int(seed),
+                                       src.data_ptr() if with_e0 else None, self.ws.data_ptr(),
+                                       self.ws_bytes, self.rec.data_ptr(), self.e_final.data_ptr(),
+                                       self.tally.data_ptr(), _stream_ptr(stream)),
+              "lim_run_batch_host")
+
+    def h2d_bytes(self) -> int:
+        return self.nshots * self.words * 4
+
+    def d2h_bytes(self) -> int:
+        return self.nshots * (RECORD_DTYPE.itemsize + 4 * self.words) + len(self.points) * TALLY_DTYPE.itemsize
+
+    def tallies(self) -> np.ndarray:
+        return np.frombuffer(self.tally.numpy().tobytes(), dtype=TALLY_DTYPE).copy()
+
+    def records(self) -> np.ndarray:
+        raw = self.rec.numpy().tobytes()[:self.nshots * RECORD_DTYPE.itemsize]
+        return np.frombuffer(raw, dtype=RECORD_DTYPE).copy()
+
+    def finals(self) -> np.ndarray:
+        a = self.e_final.numpy().view(np.uint32)[:self.nshots * self.words]
+        return a.reshape(self.nshots, self.words).copy()
+
+
 class Batch:
     """Device buffers of one ``lim_run_batch`` configuration, reusable across calls."""
 
@@ -291,13 +364,19 @@ class Batch:
         self.e_final = (torch.empty(max(self.nshots * self.words, 1), dtype=torch.int32, device=dev)
                         if e_final else None)
 
-    def run(self, seed: int, stream=None) -> None:
+    def run(self, seed: int, stream=None, e0=None) -> None:
+        """lim_run_batch, or lim_run_batch_from when ``e0`` (a device tensor of
+        nshots x final_words 32-bit words) gives the initial errors."""
         st = _stream_ptr(stream)
-        check(lib().lim_run_batch(self.ctx.handle, self.pts, len(self.points), ctypes.byref(self.prm),
-                                  int(seed), self.ws.data_ptr(), self.ws_bytes,
-                                  None if self.rec is None else self.rec.data_ptr(),
-                                  None if self.e_final is None else self.e_final.data_ptr(),
-                                  self.tally.data_ptr(), st), "lim_run_batch")
+        tail = (self.ws.data_ptr(), self.ws_bytes, None if self.rec is None else self.rec.data_ptr(),
+                None if self.e_final is None else self.e_final.data_ptr(), self.tally.data_ptr(), st)
+        if e0 is None:
+            check(lib().lim_run_batch(self.ctx.handle, self.pts, len(self.points), ctypes.byref(self.prm),
+                                      int(seed), *tail), "lim_run_batch")
+        else:
+            check(lib().lim_run_batch_from(self.ctx.handle, self.pts, len(self.points),
+                                           ctypes.byref(self.prm), int(seed), e0.data_ptr(), *tail),
+                  "lim_run_batch_from")
 
     def capture(self) -> None:
         """Capture this batch as a CUDA graph (lim_graph_create) for replay()."""

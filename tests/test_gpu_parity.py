@@ -276,6 +276,71 @@ def test_study_runner_on_rep_fig2(L, ctx):
         assert maj <= r["failures"] <= maj + ties + r["nonconverged"], r
 
 
+def _pack_rows(bits, words):
+    """0/1 rows -> rows of 32-bit words (bit v % 32 of word v // 32)."""
+    out = np.zeros((bits.shape[0], words), dtype=np.uint32)
+    for v in range(bits.shape[1]):
+        out[:, v // 32] |= bits[:, v].astype(np.uint32) << np.uint32(v % 32)
+    return out
+
+
+def test_run_from_given_errors(L, ctx):
+    """lim_run_batch_from / lim_run_batch_host: (a) the device's own noise fed
+    back gives exactly lim_run_batch's records, residuals and tallies; (b) hand-made
+    initial errors (one qubit, a row of a logical, a dense random pattern) give the
+    oracle's trajectories from the same errors; (c) the host-buffer call returns
+    the same."""
+    code = I.toric2d(8)
+    lc = ctx.from_inputs(code)
+    prm = L.params(precision="f32", tick_budget=64)
+    pts = [(lc, 0.06, 40, 0, 3), (lc, 0.1, 24, 100, 5)]
+    ref = L.Batch(ctx, pts, prm, e_final=True)
+    ref.run(9)
+    torch.cuda.synchronize()
+    words = ref.words
+    e0 = torch.zeros((ref.nshots, words), dtype=torch.int32, device="cuda")
+    row = 0
+    for (c, p, n, s0, pid) in pts:
+        e, _ = L.sample_noise(c, p, 9, pid, s0, n)
+        e0[row:row + n, :e.shape[1]] = e
+        row += n
+    got = L.Batch(ctx, pts, prm, e_final=True)
+    got.run(9, e0=e0.view(-1))
+    torch.cuda.synchronize()
+    assert np.array_equal(got.records(), ref.records())
+    assert np.array_equal(got.finals(), ref.finals())
+    assert np.array_equal(got.tallies().view(np.int64), ref.tallies().view(np.int64))
+    # (c) the same through host buffers
+    hb = L.HostBatch(ctx, pts, prm)
+    hb.e0.copy_(e0.view(-1).cpu())
+    hb.run(9)
+    assert np.array_equal(hb.records(), ref.records())
+    assert np.array_equal(hb.finals(), ref.finals())
+    assert np.array_equal(hb.tallies().view(np.int64), ref.tallies().view(np.int64))
+    hb.run(9, with_e0=False)  # noise sampled on the device
+    assert np.array_equal(hb.records(), ref.records())
+    # (b) hand-made errors against the oracle's run from the same errors
+    rng = np.random.default_rng(4)
+    n = code.n
+    bits = np.zeros((6, n), dtype=np.uint8)
+    bits[0, 17] = 1
+    bits[1, np.nonzero(code.logicals[0])[0][:5]] = 1
+    bits[2] = rng.integers(0, 2, n)
+    bits[3] = (rng.random(n) < 0.15)
+    bits[4, :] = 1
+    pts1 = [(lc, 0.0, 6, 0, 7)]
+    b1 = L.Batch(ctx, pts1, prm, e_final=True)
+    b1.run(13, e0=torch.from_numpy(_pack_rows(bits, b1.words).view(np.int32).reshape(-1)).cuda())
+    torch.cuda.synchronize()
+    rec = b1.records()
+    oc = O.OracleCode.from_code(code)
+    op = oracle_params(prm)
+    for i in range(6):
+        r = O.run_shot(oc, op, 0.0, 13, 7, i, e0=bits[i])
+        for f in ("t_clr", "converged", "failed", "moves", "ticks", "sweeps"):
+            assert rec[i][f] == r[f], (i, f, rec[i][f], r[f])
+
+
 def test_discrete_machine_on_a_quantum_code(L, ctx):
     prm = L.params(feedback="bit_discrete", precision="f32", tick_budget=60, tau=0, dt_tick=0)
     _batch_vs_oracle(L, ctx, I.toric2d(6), prm, 0.04, 100)
