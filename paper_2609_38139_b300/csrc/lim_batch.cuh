@@ -13,6 +13,9 @@ namespace lim {
 namespace batch_detail {
 
 constexpr uint8_t kNone = 0, kPending = 1, kExec = 2, kSkip = 3;
+// Scan mapping: a thread per syndrome word when the code has at least
+// team_size / kScanWordsPerThread words, else a warp per word.
+constexpr int kScanWordsPerThread = 4;
 
 // Control block of one shot (shared memory in the persistent kernel, HBM in the
 // plain path).
@@ -184,21 +187,23 @@ __device__ void shot_init(const Team &tm, const LaunchArgs &A, const DevPoint &p
     V.ctl->work[1] = 0;
   }
   tm.sync();
-  for (int w = tm.rank(); w < C.mw; w += tm.size()) {
-    uint32_t word = 0;
-    for (int b = 0; b < 32; b++) {
-      const int c = 32 * w + b;
-      if (c >= C.m) break;
-      int par = 0;
+  // s = H_X e: a warp per syndrome word, lane l computes the parity of check
+  // 32 w + l, the ballot assembles the word
+  const int lane = tm.rank() & 31;
+  for (int w = tm.rank() >> 5; w < C.mw; w += tm.size() >> 5) {
+    const int c = 32 * w + lane;
+    int par = 0;
+    if (c < C.m)
       for (int j = __ldg(C.c_ptr + c); j < __ldg(C.c_ptr + c + 1); j++) {
         const int v = __ldg(C.c_var + j);
         par ^= (V.e[v >> 5] >> (v & 31)) & 1;
       }
-      word |= (uint32_t)par << b;
+    const uint32_t word = __ballot_sync(0xffffffffu, par);
+    if (lane == 0) {
+      V.s[w] = word;
+      V.s0[w] = word;
+      if (word) atomicAdd(&V.ctl->defects, __popc(word));
     }
-    V.s[w] = word;
-    V.s0[w] = word;
-    if (word) atomicAdd(&V.ctl->defects, __popc(word));
   }
   tm.sync();
   if (A.trace_e) write_trace(tm, A, C, 0, V.e, V.s);
@@ -255,8 +260,18 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
   // --- read-out + feedback (+ the qubit half-sweep of sweep 1, which reads the
   //     same messages and does not depend on the feedback) --------------------
   if (FB == LIM_FB_CHECK_MOVE) {
-    for (int w = tm.rank(); w < C.mw; w += tm.size()) {
+    // Codes with enough syndrome words for a large part of the team: a thread
+    // per word walks the word's active checks (part of the team scans, the rest
+    // starts on the overlapped sweep).  Smaller codes: a warp per word (skipped
+    // as a whole when no check in it is active) with lane l on check 32 w + l,
+    // so the ring draws and beliefs of a word's active checks run side by side.
+    const bool by_thread = kScanWordsPerThread * C.mw >= tm.size();
+    const int lane = tm.rank() & 31;
+    const int w0 = by_thread ? tm.rank() : tm.rank() >> 5;
+    const int ws = by_thread ? tm.size() : tm.size() >> 5;
+    for (int w = w0; w < C.mw; w += ws) {
       uint32_t bits = V.s[w];
+      if (!by_thread) bits &= 1u << lane;
       while (bits) {
         const int c = 32 * w + __ffs(bits) - 1;
         bits &= bits - 1;
