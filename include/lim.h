@@ -299,8 +299,10 @@ int lim_graph_launch(lim_graph *graph, uint64_t seed, uint32_t shot_offset, void
 int lim_graph_destroy(lim_graph *graph);
 
 /* Autotuner: times the persistent kernel's launch shapes (one block or one warp
- * per shot, block sizes, blocks per SM) on a sample of the batch -- every point
- * with at most sample_shots shots and at most sample_ticks ticks -- and writes
+ * per shot, block sizes, blocks per SM, shared-memory caps) on a sample of the
+ * batch -- every point with at most sample_ticks ticks and, per shape,
+ * max(sample_shots, two shots per team of that shape / npts) shots (at most the
+ * point's own), so each shape is timed with all its teams busy -- and writes
  * the fastest into best->variant / block_threads / blocks_per_sm (the other
  * fields are copied from prm).  Results never depend on the shape (randomness
  * is keyed by shot), only speed does.  Allocates and frees its own scratch,

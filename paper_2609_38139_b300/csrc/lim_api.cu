@@ -837,12 +837,21 @@ int lim_autotune(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_pa
   return guarded([&] {
     if (!ctx || !pts || !prm || !best || npts == 0) return bad(LIM_E_INVAL, "null argument");
     if (ctx->device < 0) return bad(LIM_E_INVAL, "host-only context cannot run kernels");
+    // The sample of a shape: every point with at most sample_ticks ticks and
+    // max(sample_shots, enough shots for two per team of that shape) shots (at
+    // most the point's own), so that shapes with many small teams are timed
+    // busy, as the full batch would keep them.
     std::vector<lim_point> sample(pts, pts + npts);
-    for (auto &p : sample) {
-      p.shots = std::min(p.shots, std::max(1u, sample_shots));
-      int32_t T = p.tick_budget > 0 ? p.tick_budget : prm->tick_budget;
-      if (sample_ticks > 0) p.tick_budget = std::min(T, sample_ticks);
-    }
+    const auto make_sample = [&](size_t n_teams) {
+      const uint64_t per_point = std::max<uint64_t>(sample_shots, (2 * n_teams + npts - 1) / npts);
+      for (uint32_t i = 0; i < npts; i++) {
+        lim_point &p = sample[i];
+        p = pts[i];
+        p.shots = (uint32_t)std::min<uint64_t>(pts[i].shots, std::max<uint64_t>(1, per_point));
+        int32_t T = p.tick_budget > 0 ? p.tick_budget : prm->tick_budget;
+        if (sample_ticks > 0) p.tick_budget = std::min(T, sample_ticks);
+      }
+    };
     struct Shape {
       int variant, block, bpsm, cap;
     };
@@ -868,8 +877,12 @@ int lim_autotune(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_pa
       p.block_threads = sh.block;
       p.blocks_per_sm = sh.bpsm;
       p.smem_cap = sh.cap;
+      DevParams dp;
+      Plan pl;
+      if (derive(&p, dp) != LIM_OK || make_plan(ctx, pts, npts, &p, dp, pl) != LIM_OK) continue;  // shape does not fit
+      make_sample(pl.n_teams);
       size_t need = 0;
-      if (lim_workspace_size(ctx, sample.data(), npts, &p, &need) != LIM_OK) continue;  // shape does not fit
+      if (lim_workspace_size(ctx, sample.data(), npts, &p, &need) != LIM_OK) continue;
       if (need > ws_bytes) {
         if (ws) cudaFree(ws);
         ws = nullptr;
