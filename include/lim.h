@@ -122,7 +122,9 @@ typedef struct {
   int32_t tick_budget;     /* T, used when a point gives 0                          */
   int32_t gauge_on_move;   /* CHECK_MOVE: also gauge-switch the flipped qubit       */
   int32_t variant;         /* LIM_VARIANT_*                                         */
-  int32_t block_threads;   /* 0 = library default                                   */
+  int32_t block_threads;   /* 0 = library default: one-block teams of 512 threads,  */
+                           /* two per SM (check-centric rule) or 1024 threads, one  */
+                           /* per SM (bit-centric rule); warp teams 256 per block    */
   int32_t blocks_per_sm;   /* 0 = as many as fit                                    */
   int32_t profile;         /* 1: accumulate clock cycles per phase into the tally   */
   int32_t smem_cap;        /* CTA variant: max shared memory per block in bytes;    */
