@@ -137,7 +137,8 @@ def peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def cpu_baseline(name: str, prec: str, seconds: float = 15.0, threads: int = 0, rule: str = ""):
+def cpu_baseline(name: str, prec: str, seconds: float = 15.0, threads: int = 0, rule: str = "",
+                 sweeps: int = 0, feedback: str = ""):
     """The oracle timed on this host's cores on a bounded sample of the workload:
     shots of every point in turn (same keyed shot ids as the GPU's step 0) until
     about ``seconds`` of wall time have passed."""
@@ -146,6 +147,10 @@ def cpu_baseline(name: str, prec: str, seconds: float = 15.0, threads: int = 0, 
     w, pts = workload(name, 1)
     if rule:
         w = dict(w, rule=rule)
+    if sweeps > 0:
+        w = dict(w, K=sweeps)
+    if feedback:
+        w = dict(w, feedback=feedback)
     threads = threads or (os.cpu_count() or 1)
     codes = {}
     t0 = time.perf_counter()
@@ -192,11 +197,12 @@ def run_reference(args):
     steps = []
     for _ in range(args.warmup):
         cpu_baseline(args.workload, args.precision, seconds=max(1.0, args.ref_seconds / 4),
-                     rule=args.rule)
+                     rule=args.rule, sweeps=args.sweeps_per_tick, feedback=args.feedback)
     t0 = time.perf_counter()
     last = None
     for _ in range(args.steps):
-        last = cpu_baseline(args.workload, args.precision, seconds=args.ref_seconds, rule=args.rule)
+        last = cpu_baseline(args.workload, args.precision, seconds=args.ref_seconds, rule=args.rule,
+                            sweeps=args.sweeps_per_tick, feedback=args.feedback)
         steps.append(last)
     wall = time.perf_counter() - t0
     val = statistics.mean(s["value"] for s in steps)
@@ -231,6 +237,10 @@ def main():
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--rule", default="", help="minsum | sumproduct (default: the workload's)")
+    ap.add_argument("--feedback", default="",
+                    help="check_move | check_move_multi | bit_discrete (default: the workload's)")
+    ap.add_argument("--sweeps-per-tick", type=int, default=0,
+                    help="K (default: the workload's); relaxation alpha = dt / (K tau)")
     ap.add_argument("--smem-cap", type=int, default=0, help="max shared memory per block in bytes (0 automatic, <0 all that fits)")
     ap.add_argument("--phases", action="store_true", help="report the kernel's per-phase cycle shares")
     ap.add_argument("--autotune", action="store_true", help="pick the launch shape with lim_autotune")
@@ -263,6 +273,10 @@ def main():
     w, pts = workload(args.workload, args.shots, sizes, ps)
     if args.rule:
         w = dict(w, rule=args.rule)
+    if args.sweeps_per_tick > 0:
+        w = dict(w, K=args.sweeps_per_tick)
+    if args.feedback:
+        w = dict(w, feedback=args.feedback)
     codes = {}
     for d in pts:
         key = (d["family"], d["size"])
@@ -417,7 +431,7 @@ def main():
         line["gpu_launches"] = args.steps
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.precision, args.cpu_seconds,
-                                            rule=args.rule)
+                                            rule=args.rule, sweeps=args.sweeps_per_tick, feedback=args.feedback)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

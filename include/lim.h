@@ -62,6 +62,16 @@ extern "C" {
 /* Feedback rule. */
 #define LIM_FB_CHECK_MOVE 0   /* continuous machine: Algorithm 1, Evidence + LocalMove */
 #define LIM_FB_BIT_DISCRETE 1 /* discrete machine: f_v = 1[L_v > 0], Eq. 3-4, gauge */
+/* Continuous machine with the multi-qubit LocalMove the paper names as an
+ * alternative to the single-qubit one (a belief-guided analogue of small-set
+ * flip; the paper reports similar performance and gives no formula).  Reading
+ * used here: a ringing active check with Evidence flips the most probable
+ * odd-weight subset F of N(c) under the product of the local marginals, i.e.
+ * the odd-size F maximising sum_{v in F} L_v (odd, so the move clears c): the
+ * single-qubit pick, then further qubits of N(c) in pairs, in order of
+ * decreasing L_v (ties by CSR position), while a pair's sum is > 0.  Every
+ * qubit of F counts as one flip in the records. */
+#define LIM_FB_CHECK_MOVE_MULTI 2
 /* Ordinary BP decoding (fixed syndrome, hard decision after every iteration, stop
  * when the decision reproduces the syndrome; a tie L_v = 0 keeps the previous
  * decision) is, by the Lemma mapping the discrete machine to ordinary BP, the

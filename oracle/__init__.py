@@ -25,7 +25,7 @@ _HDR = os.path.join(_HERE, "lim_oracle.h")
 _LIB = os.path.join(_HERE, "liblim_oracle.so")
 
 RULE = {"minsum": 0, "sumproduct": 1}
-FEEDBACK = {"check_move": 0, "bit_discrete": 1}
+FEEDBACK = {"check_move": 0, "bit_discrete": 1, "check_move_multi": 2}
 PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "i16": 4, "i8": 5}
 
 
@@ -99,6 +99,8 @@ def lib() -> ctypes.CDLL:
         L.or_run_shots.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), ctypes.c_double,
                                    ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                    ctypes.c_uint32, vp]
+        L.or_multi_move_set.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+        L.or_multi_move_set.restype = ctypes.c_uint32
         L.or_bp_decode.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), ctypes.c_double,
                                    ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                    ctypes.POINTER(Record), vp]
@@ -171,6 +173,12 @@ def noise(code: OracleCode, p: float, seed: int, point: int, shot: int):
     s = np.zeros(max(code.m, 1), dtype=np.uint8)
     _check(lib().or_noise(ctypes.byref(code.struct), p, seed, point, shot, _ptr(e), _ptr(s)), "noise")
     return e, s[:code.m]
+
+
+def multi_move_set(L, first: int) -> int:
+    """Bit mask (over positions of N(c)) of the multi-qubit move for beliefs L."""
+    a = np.ascontiguousarray(L, dtype=np.float64)
+    return int(lib().or_multi_move_set(_ptr(a), len(a), int(first)))
 
 
 def bp_decode(code: OracleCode, prm: Params, p: float, seed: int, point: int, shot: int):

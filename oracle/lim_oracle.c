@@ -125,7 +125,9 @@ static int setup_wk(const or_params *prm, wk *w) {
   w->rule = prm->rule;
   if (prm->precision < OR_PREC_F64 || prm->precision > OR_PREC_I8) return OR_E_INVAL;
   if (prm->rule != OR_RULE_MINSUM && prm->rule != OR_RULE_SUMPRODUCT) return OR_E_INVAL;
-  if (prm->feedback != OR_FB_CHECK_MOVE && prm->feedback != OR_FB_BIT_DISCRETE) return OR_E_INVAL;
+  if (prm->feedback != OR_FB_CHECK_MOVE && prm->feedback != OR_FB_BIT_DISCRETE &&
+      prm->feedback != OR_FB_CHECK_MOVE_MULTI)
+    return OR_E_INVAL;
   if (!(prm->q > 0.0 && prm->q < 1.0) || !(prm->clamp > 0.0)) return OR_E_INVAL;
   if (prm->sweeps_per_tick < 1 || prm->tick_budget < 0) return OR_E_INVAL;
   w->is_int = (prm->precision == OR_PREC_I16 || prm->precision == OR_PREC_I8);
@@ -534,6 +536,26 @@ static void snap(or_trace *tr, const graph *g, int t, const uint8_t *e, const ui
 static int run(const or_code *code, const or_params *prm, double p, const uint8_t *e_given,
                uint64_t seed, uint32_t point, uint32_t shot, or_record *rec, or_trace *tr);
 
+uint32_t or_multi_move_set(const double *L, int32_t d, int32_t first) {
+  if (d < 1 || d > 32 || first < 0 || first >= d) return 0;
+  uint32_t mask = 1u << first;
+  /* the other positions by L descending, ties by position (selection order) */
+  int order[32], n = 0;
+  for (int j = 0; j < d; j++)
+    if (j != first) order[n++] = j;
+  for (int i = 0; i < n; i++)
+    for (int k = i + 1; k < n; k++)
+      if (L[order[k]] > L[order[i]] || (L[order[k]] == L[order[i]] && order[k] < order[i])) {
+        int t = order[i]; order[i] = order[k]; order[k] = t;
+      }
+  /* add pairs while they raise the log-likelihood of the set */
+  for (int i = 0; i + 1 < n; i += 2) {
+    if (!(L[order[i]] + L[order[i + 1]] > 0)) break;
+    mask |= (1u << order[i]) | (1u << order[i + 1]);
+  }
+  return mask;
+}
+
 int or_run_shot(const or_code *code, const or_params *prm, double p, uint64_t seed,
                 uint32_t point, uint32_t shot, or_record *rec, or_trace *tr) {
   return run(code, prm, p, NULL, seed, point, shot, rec, tr);
@@ -568,6 +590,10 @@ static int run(const or_code *code, const or_params *prm, double p, const uint8_
     st = OR_E_NOMEM;
     goto done;
   }
+  if (prm->feedback == OR_FB_CHECK_MOVE_MULTI && dmax > 32) { /* move sets are 32-bit masks */
+    st = OR_E_UNSUPPORTED;
+    goto done;
+  }
   if (tr) tr->n_moves = 0;
   for (int d = 0; d <= dmax; d++) theta[d] = or_theta(prm, d);
 
@@ -592,7 +618,7 @@ static int run(const or_code *code, const or_params *prm, double p, const uint8_
       readout(&w, &g, pi, cv, L);
       if (tr && tr->l_hist && t <= tr->max_ticks) memcpy(tr->l_hist + (size_t)t * n, L, (size_t)n * sizeof(double));
 
-      if (prm->feedback == OR_FB_CHECK_MOVE) {
+      if (prm->feedback == OR_FB_CHECK_MOVE || prm->feedback == OR_FB_CHECK_MOVE_MULTI) {
         /* Poisson clocks discretised per tick: each check active at the start of the
          * tick rings with probability rho; ringing checks act in the order of a
          * uniform random ring time (ties by check index). */
@@ -622,18 +648,28 @@ static int run(const or_code *code, const or_params *prm, double p, const uint8_
           for (int j = 0; j < d; j++)
             if (L[g.cvar[b + j]] == best) nt++;
           int pick = (int)(((uint64_t)rings[i].pick * (uint64_t)nt) >> 32);
-          int v = -1;
+          int first = -1;
           for (int j = 0; j < d; j++)
             if (L[g.cvar[b + j]] == best) {
-              if (pick == 0) { v = g.cvar[b + j]; break; }
+              if (pick == 0) { first = j; break; }
               pick--;
             }
-          flip_qubit(&g, e, s, v);
-          r.moves++;
-          log_move(tr, t, c, v);
-          if (prm->gauge_on_move) {
-            gauge_qubit(&g, pi, cv, vc, v);
-            L[v] = -L[v];
+          uint32_t set = 1u << first;
+          if (prm->feedback == OR_FB_CHECK_MOVE_MULTI) {
+            double Lc[32];
+            for (int j = 0; j < d; j++) Lc[j] = L[g.cvar[b + j]];
+            set = or_multi_move_set(Lc, d, first);
+          }
+          for (int j = 0; j < d; j++) {
+            if (!((set >> j) & 1)) continue;
+            const int v = g.cvar[b + j];
+            flip_qubit(&g, e, s, v);
+            r.moves++;
+            log_move(tr, t, c, v);
+            if (prm->gauge_on_move) {
+              gauge_qubit(&g, pi, cv, vc, v);
+              L[v] = -L[v];
+            }
           }
         }
       } else {

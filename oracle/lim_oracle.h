@@ -57,6 +57,7 @@ extern "C" {
 
 #define OR_FB_CHECK_MOVE 0
 #define OR_FB_BIT_DISCRETE 1
+#define OR_FB_CHECK_MOVE_MULTI 2 /* check-centric, multi-qubit move (see or_multi_move_set) */
 
 #define OR_PREC_F64 0
 #define OR_PREC_F32 1
@@ -162,6 +163,17 @@ int or_bp_sweeps(const or_code *code, const or_params *prm, const uint8_t *s, co
 /* Read-out L_v = pi_v + sum_c m_{c->v} in the oracle's precision. */
 int or_readout(const or_code *code, const or_params *prm, const double *pi, const double *cv,
                double *l_out);
+
+/* The multi-qubit LocalMove (an alternative the paper mentions beside the
+ * single-qubit move: a flip of several qubits of N(c), like small-set flip but
+ * chosen by the beliefs).  Reading: the most probable odd-weight set of N(c)
+ * under the product of the local marginals, i.e. the set F of odd size that
+ * maximises sum_{v in F} L_v; odd, so that the move clears c.  Given the beliefs
+ * L[0..d) of N(c) in CSR order and the position `first` of the single-qubit
+ * move's pick (a maximiser of L), the others are ordered by L descending (ties
+ * by position) and taken in pairs while a pair's sum is > 0.  Returns the set as
+ * a bit mask over positions. */
+uint32_t or_multi_move_set(const double *L, int32_t d, int32_t first);
 
 /* Derived scalar parameters, as the oracle computes them (for reporting). */
 typedef struct {

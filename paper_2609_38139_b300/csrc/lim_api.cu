@@ -66,7 +66,8 @@ int derive(const lim_params *p, DevParams &o) {
   if (!p) return bad(LIM_E_INVAL, "null params");
   std::memset(&o, 0, sizeof(o));
   if (p->rule != LIM_RULE_MINSUM && p->rule != LIM_RULE_SUMPRODUCT) return bad(LIM_E_INVAL, "bad rule");
-  if (p->feedback != LIM_FB_CHECK_MOVE && p->feedback != LIM_FB_BIT_DISCRETE)
+  if (p->feedback != LIM_FB_CHECK_MOVE && p->feedback != LIM_FB_BIT_DISCRETE &&
+      p->feedback != LIM_FB_CHECK_MOVE_MULTI)
     return bad(LIM_E_INVAL, "bad feedback");
   if (p->precision < LIM_PREC_F32 || p->precision > LIM_PREC_I8) return bad(LIM_E_INVAL, "bad precision");
   const bool is_int = p->precision == LIM_PREC_I16 || p->precision == LIM_PREC_I8;
@@ -80,10 +81,12 @@ int derive(const lim_params *p, DevParams &o) {
   if (p->tau > 0.0 && p->dt_tick > 0.0) alpha = p->dt_tick / (p->sweeps_per_tick * p->tau);
   if (!(alpha > 0.0 && alpha <= 1.0)) return bad(LIM_E_INVAL, "alpha = dt/(K tau) must be in (0,1]");
   o.rule = p->rule;
-  o.feedback = p->feedback;
+  // the multi-qubit move runs in the check-centric kernels, switched by a flag
+  o.multi = p->feedback == LIM_FB_CHECK_MOVE_MULTI;
+  o.feedback = o.multi ? LIM_FB_CHECK_MOVE : p->feedback;
   o.prec = p->precision;
   o.K = p->sweeps_per_tick;
-  o.gauge_on_move = (p->feedback == LIM_FB_CHECK_MOVE) && p->gauge_on_move ? 1 : 0;
+  o.gauge_on_move = (o.feedback == LIM_FB_CHECK_MOVE) && p->gauge_on_move ? 1 : 0;
   o.alpha_is_one = alpha == 1.0;
   o.profile = p->profile ? 1 : 0;
   const double pi = std::log(p->q / (1.0 - p->q));

@@ -218,6 +218,44 @@ __device__ void shot_init(const Team &tm, const LaunchArgs &A, const DevPoint &p
   }
 }
 
+// The multi-qubit move's set (a bit mask over the positions of N(c)): the
+// single-qubit pick `first`, then the remaining qubits two at a time in order of
+// decreasing belief (ties by position) while a pair's belief sum is > 0 -- the
+// odd-size subset of N(c) with the largest sum of LLRs.
+template <class A>
+__device__ __forceinline__ uint32_t multi_move_set(const A (&Lv)[kMaxDeg], int d, int first) {
+  uint32_t m = 1u << first;
+#pragma unroll 1
+  for (int it = 0; it < kMaxDeg / 2; it++) {
+    int b1 = -1, b2 = -1;
+    A v1 = A(0), v2 = A(0);
+#pragma unroll
+    for (int j = 0; j < kMaxDeg; j++)
+      if (j < d && !((m >> j) & 1) && (b1 < 0 || Lv[j] > v1)) {
+        b1 = j;
+        v1 = Lv[j];
+      }
+#pragma unroll
+    for (int j = 0; j < kMaxDeg; j++)
+      if (j < d && j != b1 && !((m >> j) & 1) && (b2 < 0 || Lv[j] > v2)) {
+        b2 = j;
+        v2 = Lv[j];
+      }
+    if (b2 < 0 || !(v1 + v2 > A(0))) break;
+    m |= (1u << b1) | (1u << b2);
+  }
+  return m;
+}
+
+// Whether the move of check c2 with set `set` (positions of N(c2)) flips qubit u.
+__device__ __forceinline__ bool move_flips(const DevCode &C, int c2, uint32_t set, int u) {
+  const int b = C.dc_u ? c2 * C.dc_u : __ldg(C.c_ptr + c2);
+  const int e = C.dc_u ? b + C.dc_u : __ldg(C.c_ptr + c2 + 1);
+  for (int j = b; j < e; j++)
+    if (__ldg(C.c_var + j) == u) return (set >> (j - b)) & 1;
+  return false;
+}
+
 // --- one tick: read-out, feedback, termination test, K sweeps ------------------
 // Returns true when the shot has ended at this tick (syndrome cleared, or the
 // budget reached).  Every thread of the team returns the same value.
@@ -302,20 +340,35 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
         for (int j = 0; j < kMaxDeg; j++)
           if (j < d && Lv[j] == best) nt++;
         int pick = (int)(((uint64_t)u.z * (uint64_t)nt) >> 32);
-        int vstar = -1;
+        int vstar = -1, first = -1;
 #pragma unroll
         for (int j = 0; j < kMaxDeg; j++) {
           if (j < d && Lv[j] == best) {
-            if (pick == 0 && vstar < 0) vstar = __ldg(C.c_var + cb + j);
+            if (pick == 0 && vstar < 0) {
+              vstar = __ldg(C.c_var + cb + j);
+              first = j;
+            }
             pick--;
           }
         }
         const int idx = atomicAdd(&ctl->ncand, 1);
         V.clist[idx] = c;
         V.cprio[c] = u.y;
-        V.ctgt[c] = vstar;
         V.cstate[c] = kPending;
-        atomicOr(V.tb + (vstar >> 5), 1u << (vstar & 31));
+        if (!P.multi) {
+          V.ctgt[c] = vstar;
+          atomicOr(V.tb + (vstar >> 5), 1u << (vstar & 31));
+        } else {
+          // the multi-qubit move: its set as a mask over the positions of N(c)
+          const uint32_t set = multi_move_set<Acc>(Lv, d, first);
+          V.ctgt[c] = (int32_t)set;
+#pragma unroll
+          for (int j = 0; j < kMaxDeg; j++)
+            if (j < d && ((set >> j) & 1)) {
+              const int v = __ldg(C.c_var + cb + j);
+              atomicOr(V.tb + (v >> 5), 1u << (v & 31));
+            }
+        }
       }
     }
     if (t < pt.T && !fused) var_pass<PREC, false>(tm.rank(), tm.size(), C, P, CV, VCc, VCn, F);
@@ -368,7 +421,12 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
                 const int c2 = __ldg(C.v_chk + q);
                 if (c2 == c) continue;
                 const uint8_t st2 = V.cstate[c2];
-                if (st2 == kNone || V.ctgt[c2] != u) continue;
+                if (st2 == kNone) continue;
+                if (!P.multi) {
+                  if (V.ctgt[c2] != u) continue;
+                } else if (!move_flips(C, c2, (uint32_t)V.ctgt[c2], u)) {
+                  continue;
+                }
                 const uint32_t p2 = V.cprio[c2];
                 if (p2 < pc || (p2 == pc && c2 < c)) {
                   if (st2 == kPending) ready = 0;
@@ -387,10 +445,21 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
         }
         for (int j = tm.rank(); j < nc; j += tm.size()) {
           const int c = V.clist[j];
-          const int v = V.ctgt[c];
-          if (V.cstate[c] == kExec) flip_bits(C, F, v);
+          const bool exec = V.cstate[c] == kExec;
           V.cstate[c] = kNone;
-          atomicAnd(V.tb + (v >> 5), ~(1u << (v & 31)));
+          if (!P.multi) {
+            const int v = V.ctgt[c];
+            if (exec) flip_bits(C, F, v);
+            atomicAnd(V.tb + (v >> 5), ~(1u << (v & 31)));
+          } else {
+            const uint32_t set = (uint32_t)V.ctgt[c];
+            const int cb = __ldg(C.c_ptr + c);
+            for (uint32_t bits = set; bits; bits &= bits - 1) {
+              const int v = __ldg(C.c_var + cb + __ffs(bits) - 1);
+              if (exec) flip_bits(C, F, v);
+              atomicAnd(V.tb + (v >> 5), ~(1u << (v & 31)));
+            }
+          }
         }
       } else if (tm.rank() == 0) {
         // With the gauge switch on every move, a flip changes later beliefs:
@@ -424,17 +493,21 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
           for (int j = 0; j < d; j++)
             if (Lv[j] == best) nt++;
           int pick = (int)(((uint64_t)(uint32_t)V.ctgt[c] * (uint64_t)nt) >> 32);
-          int vstar = -1;
+          int first = -1;
           for (int j = 0; j < d; j++)
             if (Lv[j] == best) {
               if (pick == 0) {
-                vstar = __ldg(C.c_var + cb + j);
+                first = j;
                 break;
               }
               pick--;
             }
-          flip_bits(C, F, vstar);
-          V.sg[vstar >> 5] ^= 1u << (vstar & 31);
+          const uint32_t set = P.multi ? multi_move_set<Acc>(Lv, d, first) : 1u << first;
+          for (uint32_t bits = set; bits; bits &= bits - 1) {
+            const int v = __ldg(C.c_var + cb + __ffs(bits) - 1);
+            flip_bits(C, F, v);
+            V.sg[v >> 5] ^= 1u << (v & 31);
+          }
         }
       }
       tm.sync();

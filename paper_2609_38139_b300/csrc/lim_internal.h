@@ -56,6 +56,7 @@ struct DevPoint {
 struct DevParams {
   int32_t rule, feedback, prec, K, gauge_on_move;
   int32_t alpha_is_one, profile;
+  int32_t multi;                 // check-centric rule with the multi-qubit move
   float pi_f, clamp_f, alpha_f;
   int32_t pi_q, clamp_q, A;
   float theta_f[kMaxDeg + 1];    // evidence threshold by check degree

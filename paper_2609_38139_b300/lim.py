@@ -20,7 +20,7 @@ LIM_OK = 0
 STATUS = {0: "LIM_OK", 1: "LIM_E_INVAL", 2: "LIM_E_NOMEM", 3: "LIM_E_CUDA", 4: "LIM_E_TIMEOUT",
           5: "LIM_E_NOT_CSS", 6: "LIM_E_UNSUPPORTED"}
 RULE = {"minsum": 0, "sumproduct": 1}
-FEEDBACK = {"check_move": 0, "bit_discrete": 1}
+FEEDBACK = {"check_move": 0, "bit_discrete": 1, "check_move_multi": 2}
 PREC = {"f32": 1, "f16": 2, "bf16": 3, "i16": 4, "i8": 5}
 VARIANT = {"auto": 0, "cta": 1, "warp": 2, "plain": 3}
 SECTOR = {"point": 0, "membrane": 1}

@@ -30,10 +30,11 @@ from . import inputs as I
 from . import lim
 
 
-def workload_params(w: dict, precision: str = "f32", rule: str = "") -> lim.Params:
+def workload_params(w: dict, precision: str = "f32", rule: str = "", feedback: str = "") -> lim.Params:
     rule = rule or w.get("rule", "minsum")
     qs = 0.25 if precision == "i8" else 2.0 ** -6
-    return lim.params(rule=rule, feedback=w.get("feedback", "check_move"), precision=precision,
+    return lim.params(rule=rule, feedback=feedback or w.get("feedback", "check_move"),
+                      precision=precision,
                       quant_scale=qs, q=w["q"], clamp=w["clamp"], tau=w["tau"],
                       dt_tick=w["dt_tick"], sweeps_per_tick=w["K"], tick_budget=1)
 
@@ -57,13 +58,15 @@ def point_stats(t: np.void, dt_tick: float) -> Dict[str, float]:
 
 def run_study(ctx: lim.Context, name: str, precision: str = "f32", rule: str = "",
               max_shots: int = 20000, max_failures: int = 100, batch_shots: int = 1000,
-              seed: int = 0, sizes: Sequence = (), ps: Sequence[float] = ()) -> List[dict]:
+              seed: int = 0, sizes: Sequence = (), ps: Sequence[float] = (),
+              feedback: str = "") -> List[dict]:
     """Adaptive Monte Carlo over every (size, p) point of workload ``name``: all
     unfinished points run together, ``batch_shots`` fresh shot ids per point per
     launch, until each has ``max_shots`` shots or ``max_failures`` failures."""
     w = I.WORKLOADS[name]
     rule = rule or w.get("rule", "minsum")
-    prm = workload_params(w, precision, rule)
+    feedback = feedback or w.get("feedback", "check_move")
+    prm = workload_params(w, precision, rule, feedback)
     codes, pts, meta = {}, [], []
     for fam, size, p, pid in I.workload_points(name):
         if sizes and size not in sizes:
@@ -83,6 +86,7 @@ def run_study(ctx: lim.Context, name: str, precision: str = "f32", rule: str = "
         c = codes[size]
         r = {"workload": name, "family": fam, "size": size, "n": c.n, "k": c.k, "p": p,
              "point_id": pid, "tick_budget": T, "precision": precision, "rule": rule,
+             "feedback": feedback,
              "tau": w["tau"], "dt_tick": w["dt_tick"], "seed": seed}
         r.update(point_stats(t, w["dt_tick"]))
         rows.append(r)
@@ -140,6 +144,8 @@ def main(argv=None) -> int:
     ap.add_argument("--workload", required=True, choices=sorted(I.WORKLOADS))
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--rule", default="", help="minsum | sumproduct (default: the workload's)")
+    ap.add_argument("--feedback", default="",
+                    help="check_move | check_move_multi | bit_discrete (default: the workload's)")
     ap.add_argument("--max-shots", type=int, default=20000)
     ap.add_argument("--max-failures", type=int, default=100)
     ap.add_argument("--batch-shots", type=int, default=1000)
@@ -154,7 +160,7 @@ def main(argv=None) -> int:
         allowed = {str(s): s for s in I.WORKLOADS[a.workload]["sizes"]}
         sizes = [allowed[s] for s in a.sizes.split(",")]
     rows = run_study(ctx, a.workload, a.precision, a.rule, a.max_shots, a.max_failures,
-                     a.batch_shots, a.seed, sizes)
+                     a.batch_shots, a.seed, sizes, feedback=a.feedback)
     out = open(a.out, "w") if a.out else sys.stdout
     for r in rows:
         out.write(json.dumps(r) + "\n")

@@ -341,6 +341,24 @@ def test_run_from_given_errors(L, ctx):
             assert rec[i][f] == r[f], (i, f, rec[i][f], r[f])
 
 
+@pytest.mark.parametrize("maker,prec,q,qs,variant,gauge,dt", [
+    (lambda: I.toric2d(6), "f32", 0.05, 0, "cta", 0, 0.1),
+    (lambda: I.toric2d(6), "f32", 0.05, 0, "warp", 1, 0.1),
+    (lambda: I.toric3d_membrane(4), "i16", 0.125, 2 ** -6, "cta", 0, 0.1),
+    (lambda: I.toric3d_membrane(3), "i16", 0.125, 2 ** -6, "warp", 0, 0.01),
+    (lambda: I.bb_code(6, 6), "i8", 0.05, 0.25, "warp", 0, 0.1),
+    (lambda: I.bb_code(12, 6), "f16", 0.05, 0, "cta", 0, 0.1),
+])
+def test_multi_qubit_move_trajectories(L, ctx, maker, prec, q, qs, variant, gauge, dt):
+    """The multi-qubit LocalMove (most probable odd-weight subset of N(c)),
+    shot by shot against the oracle: fused and relaxed sweeps, both team
+    variants, the one-thread path of the gauge switch."""
+    budget = 200 if dt == 0.1 else 2000
+    prm = L.params(feedback="check_move_multi", precision=prec, quant_scale=qs or 2 ** -6, q=q,
+                   dt_tick=dt, tick_budget=budget, variant=variant, gauge_on_move=gauge)
+    _batch_vs_oracle(L, ctx, maker(), prm, 0.08, 96, finals=(dt == 0.1))
+
+
 def test_discrete_machine_on_a_quantum_code(L, ctx):
     prm = L.params(feedback="bit_discrete", precision="f32", tick_budget=60, tau=0, dt_tick=0)
     _batch_vs_oracle(L, ctx, I.toric2d(6), prm, 0.04, 100)
@@ -468,7 +486,7 @@ def test_full_size_toric2d_sampled(L, ctx, L_, p, shots):
 
 
 @pytest.mark.parametrize("rule,fb", [("minsum", "check_move"), ("minsum", "bit_discrete"),
-                                     ("sumproduct", "check_move")])
+                                     ("sumproduct", "check_move"), ("minsum", "check_move_multi")])
 def test_plain_path_equals_batched_kernel(L, ctx, rule, fb):
     """The plain baseline (one launch per tick, host-polled termination, HBM
     state) computes the same trajectories as the persistent kernel."""

@@ -452,9 +452,62 @@ def test_ordinary_bp_decoder_clears_single_errors():
     assert found >= 5
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_multi_move_set_is_the_most_probable_odd_set(seed):
+    """The multi-qubit move flips the odd-weight subset of N(c) with the largest
+    sum of LLRs (most probable under the product of the marginals), containing
+    the single-qubit pick; brute force over all odd subsets, with ties."""
+    rng = np.random.default_rng(seed)
+    for trial in range(300):
+        d = int(rng.integers(2, 9))
+        if trial % 2:
+            L = rng.integers(-3, 4, d).astype(np.float64)      # many ties
+        else:
+            L = rng.normal(0.0, 3.0, d)
+        best = L.max()
+        ties = np.nonzero(L == best)[0]
+        first = int(ties[rng.integers(len(ties))])
+        mask = O.multi_move_set(L, first)
+        F = [j for j in range(d) if (mask >> j) & 1]
+        assert first in F and len(F) % 2 == 1
+        opt = max(sum(L[j] for j in range(d) if (m >> j) & 1)
+                  for m in range(1, 1 << d) if bin(m).count("1") % 2 == 1)
+        assert sum(L[F]) == pytest.approx(opt, abs=1e-12), (L, first, F)
+        # no positive-sum pair left out: the set is the top of the order
+        rest = sorted((j for j in range(d) if j not in F), key=lambda j: (-L[j], j))
+        if len(rest) >= 2:
+            assert not (L[rest[0]] + L[rest[1]] > 0)
+
+
+@pytest.mark.parametrize("maker,prec", [(lambda: I.toric2d(6), "f64"),
+                                        (lambda: I.toric3d_membrane(3), "i16")])
+def test_multi_move_equals_single_move_until_a_set_is_flipped(maker, prec):
+    """The multi-qubit move contains the single-qubit pick, so a trajectory in
+    which every multi-qubit move flipped exactly one qubit is, tick by tick, the
+    single-qubit trajectory; and on these codes some moves do flip a set."""
+    code = maker()
+    oc = O.OracleCode.from_code(code)
+    q = 0.125 if "membrane" in code.name else 0.05
+    kw = dict(precision=prec, q=q, tick_budget=60)
+    a = O.params(feedback="check_move", **kw)
+    b = O.params(feedback="check_move_multi", **kw)
+    sets = 0
+    for shot in range(24):
+        rb = O.run_shot(oc, b, 0.08, 6, 2, shot, trace_ticks=60, move_cap=4096)
+        moves = [tuple(m[:2]) for m in rb["trace"]["moves"]]
+        if len(set(moves)) != len(moves):  # some (tick, check) flipped several qubits
+            sets += 1
+            continue
+        ra = O.run_shot(oc, a, 0.08, 6, 2, shot, trace_ticks=60)
+        assert np.array_equal(ra["trace"]["e_hist"], rb["trace"]["e_hist"]), shot
+        assert ra["t_clr"] == rb["t_clr"] and ra["moves"] == rb["moves"]
+    assert sets > 0
+
+
 @pytest.mark.parametrize("maker,fb,prec", [
     (lambda: I.toric2d(6), "check_move", "f64"), (lambda: I.toric3d_membrane(3), "check_move", "i16"),
-    (lambda: I.bb_code(6, 6), "check_move", "f32"), (lambda: I.rep_code(30), "bit_discrete", "i8")])
+    (lambda: I.bb_code(6, 6), "check_move", "f32"), (lambda: I.rep_code(30), "bit_discrete", "i8"),
+    (lambda: I.toric3d_membrane(3), "check_move_multi", "i16"), (lambda: I.bb_code(6, 6), "check_move_multi", "f32")])
 def test_syndrome_invariant_every_tick(maker, fb, prec):
     """s = H_X e (mod 2) after every tick (Eq. 4 and Algorithm 1's update)."""
     code = maker()
