@@ -40,6 +40,10 @@ EXPORTS = ["lim_last_error", "lim_version", "lim_ctx_create", "lim_ctx_destroy",
            "lim_trace", "lim_bp_sweeps", "lim_readout"]
 
 
+LIM_MAX_POINTS = 128  # points per lim_run_batch call (include/lim.h)
+LIM_MAX_CODES = 16    # distinct codes per call
+
+
 class LimError(RuntimeError):
     pass
 

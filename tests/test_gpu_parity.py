@@ -423,6 +423,51 @@ def test_edge_cases(L, ctx):
     assert np.all(rec["failed"] == 1) and np.all(rec["t_clr"] == 0)
 
 
+def _irregular_code(seed, n=40, m=30):
+    """A random irregular check matrix with check degrees 1..8 and qubit degrees
+    at most 8 (the library's limits), no Z checks: the X-logicals are a basis of
+    the vectors modulo row(H_X)."""
+    rng = np.random.default_rng(seed)
+    deg = np.zeros(n, dtype=int)
+    rows = []
+    for c in range(m):
+        w = int(rng.integers(1, 9))
+        free = [v for v in rng.permutation(n) if deg[v] < 8][:w]
+        for v in free:
+            deg[v] += 1
+        rows.append(sorted(int(v) for v in free))
+    rows[0] = rows[0][:1]   # keep at least one degree-1 check
+    return I.code_from_rows(f"irregular{seed}", n, rows, [])
+
+
+def test_maximum_sizes_and_irregular_codes(L, ctx):
+    """One launch at the library's limits -- LIM_MAX_CODES codes (families and
+    irregular codes with check degrees 1..8, qubit degrees up to 8) and
+    LIM_MAX_POINTS points -- equals the oracle shot by shot; one code or one
+    point more is refused."""
+    codes = [I.toric2d(5), I.toric2d(6), I.toric3d_point(3), I.toric3d_membrane(3), I.bb_code(6, 6),
+             I.rep_code(17), I.rep_code(12, periodic=True)] + [_irregular_code(s) for s in range(9)]
+    assert len(codes) == L.LIM_MAX_CODES
+    dc = max(int(np.diff(c.hx_ptr).max()) for c in codes)
+    dv = max(int(np.bincount(c.hx_col, minlength=c.n).max()) for c in codes)
+    assert dc == 8 and dv == 8
+    lcs = [ctx.from_inputs(c) for c in codes]
+    prm = L.params(precision="f32", tick_budget=40)
+    pts = [(lcs[i % 16], 0.02 + 0.01 * (i % 7), 2, 3 * i, i) for i in range(L.LIM_MAX_POINTS)]
+    tal, rec = L.run_batch(ctx, pts, prm, 21)
+    assert int(tal["errors"].sum()) == 0
+    row = 0
+    for (lc, p, n, s0, pid) in pts:
+        ora = oracle_point(codes[pid % 16], prm, p, 21, pid, s0, n)
+        compare_records(rec[row:row + n], ora, f"point {pid}")
+        row += n
+    with pytest.raises(L.LimError):
+        L.run_batch(ctx, pts + [pts[0][:4] + (999,)], prm, 21)
+    with pytest.raises(L.LimError):
+        L.run_batch(ctx, [(c, 0.05, 1, 0, i) for i, c in enumerate(lcs + [ctx.from_inputs(I.toric2d(4))])],
+                    prm, 21)
+
+
 def test_ler_f32_agrees_with_fp64_oracle(L, ctx):
     code = I.toric2d(8)
     prm = L.params(precision="f32", tick_budget=32)
