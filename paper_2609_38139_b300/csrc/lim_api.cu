@@ -238,7 +238,7 @@ int make_plan(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_param
     pl.slot_bytes = (slot + 255) & ~size_t(255);
   }
   int occ = 0;
-  int st = batch_occupancy(pl.warp, dp.prec, dp.rule, dp.feedback, pl.block, pl.smem, &occ);
+  int st = batch_occupancy(pl.warp, dp.prec, dp.rule, kernel_feedback(dp), pl.block, pl.smem, &occ);
   if (st) return st;
   if (occ < 1) return bad(LIM_E_UNSUPPORTED, "batch kernel does not fit on an SM with this shape");
   if (prm->blocks_per_sm > 0) occ = std::min(occ, prm->blocks_per_sm);
@@ -791,12 +791,12 @@ int lim_graph_create_from(lim_ctx *ctx, const lim_point *pts, uint32_t npts, con
     const void *fn = nullptr;
     if (err == cudaSuccess) {
       int occ = 0;
-      st = batch_occupancy(pl.warp, dp.prec, dp.rule, dp.feedback, pl.block, pl.smem, &occ);
+      st = batch_occupancy(pl.warp, dp.prec, dp.rule, kernel_feedback(dp), pl.block, pl.smem, &occ);
       if (st) {
         lim_graph_destroy(g);
         return st;
       }
-      fn = batch_fn_ptr(pl.warp, dp.prec, dp.rule, dp.feedback);
+      fn = batch_fn_ptr(pl.warp, dp.prec, dp.rule, kernel_feedback(dp));
       g->kargs[0] = &g->args;
       g->kp.func = const_cast<void *>(fn);
       g->kp.gridDim = dim3(pl.grid);

@@ -271,7 +271,11 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
   // Fused mode (alpha = 1, uniform qubit degree, check-centric rule): the three
   // message buffers rotate as check->qubit messages of sweeps k, k-1, k-2 and the
   // qubit->check messages are never stored; vc_sel counts the rotation.
-  const bool fused = FB == LIM_FB_CHECK_MOVE && P.alpha_is_one && fused_ok(C);
+  // FB: the feedback rule as compiled -- check-centric (single- or multi-qubit
+  // move) or bit-centric
+  constexpr bool kCheck = FB != LIM_FB_BIT_DISCRETE;
+  constexpr bool kMulti = FB == LIM_FB_CHECK_MOVE_MULTI;
+  const bool fused = kCheck && P.alpha_is_one && fused_ok(C);
   T *const B[3] = {V.CV, V.VC0, V.VC1};
   T *CV = fused ? B[R.vc_sel] : V.CV;
   T *VCc = R.vc_sel ? V.VC1 : V.VC0;
@@ -297,7 +301,7 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
   int nc = 0;
   // --- read-out + feedback (+ the qubit half-sweep of sweep 1, which reads the
   //     same messages and does not depend on the feedback) --------------------
-  if (FB == LIM_FB_CHECK_MOVE) {
+  if (kCheck) {
     // Codes with enough syndrome words for a large part of the team: a thread
     // per word walks the word's active checks (part of the team scans, the rest
     // starts on the overlapped sweep).  Smaller codes: a warp per word (skipped
@@ -355,7 +359,7 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
         V.clist[idx] = c;
         V.cprio[c] = u.y;
         V.cstate[c] = kPending;
-        if (!P.multi) {
+        if (!kMulti) {
           V.ctgt[c] = vstar;
           atomicOr(V.tb + (vstar >> 5), 1u << (vstar & 31));
         } else {
@@ -393,7 +397,7 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
   }
   tm.sync();
   clk.mark(1);
-  if (FB == LIM_FB_CHECK_MOVE) {
+  if (kCheck) {
     nc = ctl->ncand;
     if (nc > 0) {
       if (!P.gauge_on_move) {
@@ -422,7 +426,7 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
                 if (c2 == c) continue;
                 const uint8_t st2 = V.cstate[c2];
                 if (st2 == kNone) continue;
-                if (!P.multi) {
+                if (!kMulti) {
                   if (V.ctgt[c2] != u) continue;
                 } else if (!move_flips(C, c2, (uint32_t)V.ctgt[c2], u)) {
                   continue;
@@ -447,7 +451,7 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
           const int c = V.clist[j];
           const bool exec = V.cstate[c] == kExec;
           V.cstate[c] = kNone;
-          if (!P.multi) {
+          if (!kMulti) {
             const int v = V.ctgt[c];
             if (exec) flip_bits(C, F, v);
             atomicAnd(V.tb + (v >> 5), ~(1u << (v & 31)));
@@ -502,7 +506,7 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
               }
               pick--;
             }
-          const uint32_t set = P.multi ? multi_move_set<Acc>(Lv, d, first) : 1u << first;
+          const uint32_t set = kMulti ? multi_move_set<Acc>(Lv, d, first) : 1u << first;
           for (uint32_t bits = set; bits; bits &= bits - 1) {
             const int v = __ldg(C.c_var + cb + __ffs(bits) - 1);
             flip_bits(C, F, v);
@@ -751,16 +755,28 @@ __global__ void __launch_bounds__(1024) plain_finish_kernel(const __grid_constan
   shot_finish<TeamCTA, PREC>(tm, A, 0, C, pt.item0 + blockIdx.x, V, R);
 }
 
+template <class Team, int PREC, int RULE>
+const void *pick_kernel_fb(int fb) {
+  if (fb == LIM_FB_CHECK_MOVE) return (const void *)batch_kernel<Team, PREC, RULE, LIM_FB_CHECK_MOVE>;
+  if (fb == LIM_FB_CHECK_MOVE_MULTI)
+    return (const void *)batch_kernel<Team, PREC, RULE, LIM_FB_CHECK_MOVE_MULTI>;
+  return (const void *)batch_kernel<Team, PREC, RULE, LIM_FB_BIT_DISCRETE>;
+}
+
+// The persistent kernel for (rule, feedback as compiled: LIM_FB_*).
 template <class Team, int PREC>
 const void *pick_kernel(int rule, int fb) {
-  if (rule == LIM_RULE_SUMPRODUCT && !MT<PREC>::is_int) {
-    return fb == LIM_FB_CHECK_MOVE
-               ? (const void *)batch_kernel<Team, PREC, LIM_RULE_SUMPRODUCT, LIM_FB_CHECK_MOVE>
-               : (const void *)batch_kernel<Team, PREC, LIM_RULE_SUMPRODUCT, LIM_FB_BIT_DISCRETE>;
-  }
-  return fb == LIM_FB_CHECK_MOVE
-             ? (const void *)batch_kernel<Team, PREC, LIM_RULE_MINSUM, LIM_FB_CHECK_MOVE>
-             : (const void *)batch_kernel<Team, PREC, LIM_RULE_MINSUM, LIM_FB_BIT_DISCRETE>;
+  if (rule == LIM_RULE_SUMPRODUCT && !MT<PREC>::is_int)
+    return pick_kernel_fb<Team, PREC, LIM_RULE_SUMPRODUCT>(fb);
+  return pick_kernel_fb<Team, PREC, LIM_RULE_MINSUM>(fb);
+}
+
+template <int PREC, int RULE>
+const void *pick_plain_tick(int fb) {
+  if (fb == LIM_FB_CHECK_MOVE) return (const void *)plain_tick_kernel<PREC, RULE, LIM_FB_CHECK_MOVE>;
+  if (fb == LIM_FB_CHECK_MOVE_MULTI)
+    return (const void *)plain_tick_kernel<PREC, RULE, LIM_FB_CHECK_MOVE_MULTI>;
+  return (const void *)plain_tick_kernel<PREC, RULE, LIM_FB_BIT_DISCRETE>;
 }
 
 // The three plain kernels for (rule, feedback): init, tick, finish.
@@ -769,13 +785,9 @@ void pick_plain(int rule, int fb, const void **init, const void **tick, const vo
   *init = (const void *)plain_init_kernel<PREC>;
   *finish = (const void *)plain_finish_kernel<PREC>;
   if (rule == LIM_RULE_SUMPRODUCT && !MT<PREC>::is_int)
-    *tick = fb == LIM_FB_CHECK_MOVE
-                ? (const void *)plain_tick_kernel<PREC, LIM_RULE_SUMPRODUCT, LIM_FB_CHECK_MOVE>
-                : (const void *)plain_tick_kernel<PREC, LIM_RULE_SUMPRODUCT, LIM_FB_BIT_DISCRETE>;
+    *tick = pick_plain_tick<PREC, LIM_RULE_SUMPRODUCT>(fb);
   else
-    *tick = fb == LIM_FB_CHECK_MOVE
-                ? (const void *)plain_tick_kernel<PREC, LIM_RULE_MINSUM, LIM_FB_CHECK_MOVE>
-                : (const void *)plain_tick_kernel<PREC, LIM_RULE_MINSUM, LIM_FB_BIT_DISCRETE>;
+    *tick = pick_plain_tick<PREC, LIM_RULE_MINSUM>(fb);
 }
 
 }  // namespace batch_detail

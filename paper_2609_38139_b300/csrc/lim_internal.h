@@ -95,6 +95,9 @@ struct CodeLayout {
 };
 
 size_t msg_bytes(int prec);
+// The feedback rule the kernels are compiled for: the multi-qubit move has its
+// own instantiation of the check-centric kernels.
+LIM_HD inline int kernel_feedback(const DevParams &P) { return P.multi ? LIM_FB_CHECK_MOVE_MULTI : P.feedback; }
 CodeLayout code_layout(const DevCode &c, int prec);
 
 // Host-side code object.

@@ -136,7 +136,7 @@ int batch_occupancy(int warp, int prec, int rule, int fb, int block, size_t smem
 }
 
 int launch_batch(const LaunchArgs &args, int warp, int grid, int block, size_t smem, void *stream) {
-  const void *fn = batch_fn(warp, args.prm.prec, args.prm.rule, args.prm.feedback);
+  const void *fn = batch_fn(warp, args.prm.prec, args.prm.rule, kernel_feedback(args.prm));
   if (!fn) {
     set_error("no kernel for this precision/rule/feedback");
     return LIM_E_UNSUPPORTED;
@@ -161,7 +161,7 @@ int launch_plain(const LaunchArgs &args, int kind, int t, int *running, int grid
     return LIM_E_UNSUPPORTED;
   }
   const void *fi, *ft, *ff;
-  plain_fns_f32(args.prm.rule, args.prm.feedback, &fi, &ft, &ff);
+  plain_fns_f32(args.prm.rule, kernel_feedback(args.prm), &fi, &ft, &ff);
   const void *fn = kind == 0 ? fi : (kind == 1 ? ft : ff);
   void *p_args[] = {const_cast<LaunchArgs *>(&args)};
   void *p_tick[] = {const_cast<LaunchArgs *>(&args), &t, &running};
