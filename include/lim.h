@@ -53,7 +53,7 @@ extern "C" {
 #define LIM_E_CUDA 3        /* a CUDA runtime call failed                             */
 #define LIM_E_TIMEOUT 4     /* a device-side bounded loop gave up                     */
 #define LIM_E_NOT_CSS 5     /* H_Z H_X^T != 0                                         */
-#define LIM_E_UNSUPPORTED 6 /* valid request outside what this build supports         */
+#define LIM_E_UNSUPPORTED 6 /* valid request outside what the library supports       */
 
 /* Check-node rule of Eq. 2. */
 #define LIM_RULE_MINSUM 0     /* sign product times minimum magnitude             */
