@@ -112,6 +112,20 @@ def fit_clear_time(sizes: Sequence[float], means: Sequence[float], form: str = "
     return float(a), float(b), float(np.sqrt(np.mean(res * res)))
 
 
+def fit_slope(sizes: Sequence[float], lers: Sequence[float], p: float, p_th: float):
+    """Fig. S1(b): the slope alpha(p) of p_L = A(p) (p / p_th)^(alpha(p) d) at one p,
+    from a least-squares line through log p_L against the distance d.  Returns
+    (alpha, log A, rms residual of log p_L); points with p_L = 0 are left out."""
+    d = np.asarray([x for x, y in zip(sizes, lers) if y > 0], dtype=np.float64)
+    y = np.log(np.asarray([y for y in lers if y > 0], dtype=np.float64))
+    if len(d) < 2:
+        raise ValueError("need two sizes with failures")
+    A = np.stack([d, np.ones_like(d)], axis=1)
+    (slope, logA), *_ = np.linalg.lstsq(A, y, rcond=None)
+    res = y - (slope * d + logA)
+    return float(slope / math.log(p / p_th)), float(logA), float(np.sqrt(np.mean(res * res)))
+
+
 def crossings(rows: List[dict]) -> List[dict]:
     """Where the LER curves of consecutive sizes cross: for each pair of sizes,
     the p at which log LER(small) - log LER(large) changes sign (linear

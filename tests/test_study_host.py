@@ -63,3 +63,14 @@ def test_crossings_locate_a_threshold():
     cr = S.crossings(rows)
     assert len(cr) == 1 and cr[0]["sizes"] == [8, 16]
     assert cr[0]["p_cross"] == pytest.approx(0.08, abs=1e-9)
+
+
+def test_slope_fit_recovers_alpha():
+    """p_L = A (p / p_th)^(alpha d) exactly: the fit returns alpha and log A."""
+    d = np.array([8, 12, 16, 24], dtype=float)
+    for p, alpha in ((0.04, 0.25), (0.06, 0.4)):
+        lers = 0.3 * (p / 0.08) ** (alpha * d)
+        a, logA, res = S.fit_slope(d, lers, p, 0.08)
+        assert a == pytest.approx(alpha) and logA == pytest.approx(math.log(0.3)) and res < 1e-12
+    with pytest.raises(ValueError):
+        S.fit_slope([8, 12], [0.0, 0.1], 0.04, 0.08)
