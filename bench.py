@@ -190,10 +190,30 @@ def cpu_baseline(name: str, prec: str, seconds: float = 15.0, threads: int = 0, 
                       f"as the GPU's first step), {prec} oracle, {dt:.1f} s wall"}
 
 
+def arm_config(args, w, npoints: int) -> dict:
+    """The workload as both arms describe it in their JSON lines."""
+    return {"workload": args.workload, "codes": f"{w['family']} sizes {w['sizes']}",
+            "points": npoints, "shots_per_point_per_step": args.shots,
+            "shots_per_step": args.shots * npoints,
+            "rule": w.get("rule", "minsum"), "feedback": w.get("feedback", "check_move"),
+            "tau": w["tau"], "dt_tick": w["dt_tick"], "sweeps_per_tick": w.get("K", 1),
+            "tick_budget": w["budget"], "variant": args.variant,
+            "l2": "flushed between steps (256 MiB write, outside the timed window)"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.shots <= 0:
+        args.shots = I.WORKLOADS[args.workload].get("bench_shots", 32)
+    w = dict(I.WORKLOADS[args.workload])
+    for key, val in (("rule", args.rule), ("feedback", args.feedback)):
+        if val:
+            w[key] = val
+    if args.sweeps_per_tick > 0:
+        w["K"] = args.sweeps_per_tick
+    npts = len(I.workload_points(args.workload))
     steps = []
     for _ in range(args.warmup):
         cpu_baseline(args.workload, args.precision, seconds=max(1.0, args.ref_seconds / 4),
@@ -210,7 +230,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * wall / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": args.workload, "parallelism": "host threads"},
+            "config": dict(arm_config(args, w, npts), parallelism="host threads",
+                           launch_shape="oracle, shots of every point in turn"),
             "cpu_baseline": {"value": val, "unit": "shot-ticks/s", "cores": last["cores"],
                              "kind": "oracle", "sample": last["sample"]},
             "e2e": {"value": val, "unit": "shot-ticks/s", "h2d_bytes_per_step": 0,
@@ -362,17 +383,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": args.workload, "codes": f"{w['family']} sizes {w['sizes']}",
-                       "points": len(pts), "shots_per_point_per_step": args.shots,
-                       "shots_per_step": shots // max(1, args.steps) // world,
-                       "rule": w.get("rule", "minsum"),
-                       "feedback": w.get("feedback", "check_move"),
-                       "tau": w["tau"], "dt_tick": w["dt_tick"],
-                       "sweeps_per_tick": w.get("K", 1), "tick_budget": w["budget"],
-                       "variant": args.variant,
-                       "l2": "flushed between steps (256 MiB write, outside the timed window)",
-                       "parallelism": f"replicas x{world}, disjoint shot ids",
-                       "launch_shape": tuned or "library default"},
+            "config": dict(arm_config(args, w, len(pts)),
+                           parallelism=f"replicas x{world}, disjoint shot ids",
+                           launch_shape=tuned or "library default"),
             "msg_updates_per_s": upd_rate,
             "ler_sample": fails / max(1, shots),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
