@@ -669,7 +669,7 @@ __device__ __noinline__ void fused_run(int rank, int size, const DevCode &C, con
   // checks in flight per thread: wide rows (BB, membrane: 12 gathered values)
   // one at a time, which keeps the warp-team kernel's spills down (BB +11 %)
   constexpr int NB = SMEM ? (NP <= 6 ? 2 : 1) : (NP <= 4 ? 4 : (NP <= 6 ? 2 : 1));
-  if (work && (!SMEM || C.m >= 4 * size)) fused_loop_dyn<PREC, RULE, DC, DV, NB>(work, C, P, sbit, CVp, CVn);
+  if (work && (!SMEM || C.m >= 2 * size)) fused_loop_dyn<PREC, RULE, DC, DV, NB>(work, C, P, sbit, CVp, CVn);
   else fused_loop<PREC, RULE, DC, DV, NB>(rank, size, C, P, sbit, CVp, CVn);
 }
 
