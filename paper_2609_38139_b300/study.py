@@ -166,6 +166,8 @@ def main(argv=None) -> int:
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--sizes", default="", help="comma-separated subset of sizes")
     ap.add_argument("--device", type=int, default=0)
+    ap.add_argument("--p-th", type=float, default=0.0,
+                    help="threshold for the slope fits (default: mean of the crossings)")
     ap.add_argument("--out", default="")
     a = ap.parse_args(argv)
     ctx = lim.Context(a.device)
@@ -179,6 +181,16 @@ def main(argv=None) -> int:
     for r in rows:
         out.write(json.dumps(r) + "\n")
     summ = {"workload": a.workload, "crossings": crossings(rows)}
+    p_th = a.p_th or (float(np.mean([c["p_cross"] for c in summ["crossings"]]))
+                      if summ["crossings"] else 0.0)
+    if p_th > 0 and all(not isinstance(r["size"], (list, tuple)) for r in rows):
+        summ["p_th_for_slopes"] = p_th
+        summ["slopes"] = []
+        for p in sorted({r["p"] for r in rows}):
+            rr = [r for r in rows if r["p"] == p]
+            if p < p_th and sum(r["failures"] > 0 for r in rr) >= 2:
+                al, logA, res = fit_slope([r["size"] for r in rr], [r["ler"] for r in rr], p, p_th)
+                summ["slopes"].append({"p": p, "alpha": al, "log_A": logA, "rms": res})
     out.write(json.dumps(summ) + "\n")
     if a.out:
         out.close()
