@@ -153,6 +153,24 @@ def crossings(rows: List[dict]) -> List[dict]:
     return out
 
 
+def summarize(rows: List[dict], p_th: float = 0.0) -> dict:
+    """Crossings of the LER curves and, below the threshold (p_th, else the mean
+    crossing), the slope fits alpha(p) for codes with a scalar size."""
+    summ = {"crossings": crossings(rows)}
+    if not p_th and summ["crossings"]:
+        p_th = float(np.mean([c["p_cross"] for c in summ["crossings"]]))
+    if p_th > 0 and all(not isinstance(r["size"], (list, tuple)) for r in rows):
+        summ["p_th_for_slopes"] = p_th
+        summ["slopes"] = []
+        for p in sorted({r["p"] for r in rows}):
+            rr = [r for r in rows if r["p"] == p]
+            # alpha divides by log(p / p_th): only points clearly below the threshold
+            if p < 0.99 * p_th and sum(r["failures"] > 0 for r in rr) >= 2:
+                al, logA, res = fit_slope([r["size"] for r in rr], [r["ler"] for r in rr], p, p_th)
+                summ["slopes"].append({"p": p, "alpha": al, "log_A": logA, "rms": res})
+    return summ
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--workload", required=True, choices=sorted(I.WORKLOADS))
@@ -180,17 +198,7 @@ def main(argv=None) -> int:
     out = open(a.out, "w") if a.out else sys.stdout
     for r in rows:
         out.write(json.dumps(r) + "\n")
-    summ = {"workload": a.workload, "crossings": crossings(rows)}
-    p_th = a.p_th or (float(np.mean([c["p_cross"] for c in summ["crossings"]]))
-                      if summ["crossings"] else 0.0)
-    if p_th > 0 and all(not isinstance(r["size"], (list, tuple)) for r in rows):
-        summ["p_th_for_slopes"] = p_th
-        summ["slopes"] = []
-        for p in sorted({r["p"] for r in rows}):
-            rr = [r for r in rows if r["p"] == p]
-            if p < p_th and sum(r["failures"] > 0 for r in rr) >= 2:
-                al, logA, res = fit_slope([r["size"] for r in rr], [r["ler"] for r in rr], p, p_th)
-                summ["slopes"].append({"p": p, "alpha": al, "log_A": logA, "rms": res})
+    summ = dict(summarize(rows, a.p_th), workload=a.workload)
     out.write(json.dumps(summ) + "\n")
     if a.out:
         out.close()

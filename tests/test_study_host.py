@@ -74,3 +74,20 @@ def test_slope_fit_recovers_alpha():
         assert a == pytest.approx(alpha) and logA == pytest.approx(math.log(0.3)) and res < 1e-12
     with pytest.raises(ValueError):
         S.fit_slope([8, 12], [0.0, 0.1], 0.04, 0.08)
+
+
+def test_summary_of_synthetic_curves():
+    """Curves 0.5 (p / 0.08)^(0.3 d): one crossing at 0.08 per pair of sizes, and
+    the slope fits below it return alpha = 0.3."""
+    rows = []
+    for d in (8, 12, 16):
+        for p in np.linspace(0.04, 0.12, 9):
+            ler = 0.5 * (p / 0.08) ** (0.3 * d)
+            rows.append({"size": d, "n": 2 * d * d, "p": float(p), "ler": ler,
+                         "failures": 10})
+    summ = S.summarize(rows)
+    assert [c["sizes"] for c in summ["crossings"]] == [[8, 12], [12, 16]]
+    assert summ["p_th_for_slopes"] == pytest.approx(0.08, abs=1e-9)
+    assert len(summ["slopes"]) == 4
+    for sl in summ["slopes"]:
+        assert sl["alpha"] == pytest.approx(0.3, rel=1e-6)
