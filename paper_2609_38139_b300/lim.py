@@ -382,14 +382,21 @@ class Batch:
                                            ctypes.byref(self.prm), int(seed), e0.data_ptr(), *tail),
                   "lim_run_batch_from")
 
-    def capture(self) -> None:
-        """Capture this batch as a CUDA graph (lim_graph_create) for replay()."""
+    def capture(self, e0=None) -> None:
+        """Capture this batch as a CUDA graph (lim_graph_create) for replay(); with
+        ``e0`` (a device tensor the caller refills between replays) the shots start
+        from those errors (lim_graph_create_from)."""
         h = ctypes.c_void_p()
-        check(lib().lim_graph_create(self.ctx.handle, self.pts, len(self.points), ctypes.byref(self.prm),
-                                     self.ws.data_ptr(), self.ws_bytes,
-                                     None if self.rec is None else self.rec.data_ptr(),
-                                     None if self.e_final is None else self.e_final.data_ptr(),
-                                     self.tally.data_ptr(), ctypes.byref(h)), "lim_graph_create")
+        tail = (self.ws.data_ptr(), self.ws_bytes, None if self.rec is None else self.rec.data_ptr(),
+                None if self.e_final is None else self.e_final.data_ptr(), self.tally.data_ptr(),
+                ctypes.byref(h))
+        if e0 is None:
+            check(lib().lim_graph_create(self.ctx.handle, self.pts, len(self.points),
+                                         ctypes.byref(self.prm), *tail), "lim_graph_create")
+        else:
+            check(lib().lim_graph_create_from(self.ctx.handle, self.pts, len(self.points),
+                                              ctypes.byref(self.prm), e0.data_ptr(), *tail),
+                  "lim_graph_create_from")
         self.graph = h
 
     def replay(self, seed: int, shot_offset: int, stream=None) -> None:

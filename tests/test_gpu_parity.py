@@ -359,6 +359,30 @@ def test_multi_qubit_move_trajectories(L, ctx, maker, prec, q, qs, variant, gaug
     _batch_vs_oracle(L, ctx, maker(), prm, 0.08, 96, finals=(dt == 0.1))
 
 
+def test_graph_replay_from_given_errors(L, ctx):
+    """lim_graph_create_from: a graph captured over a device error buffer, replayed
+    after refilling the buffer, equals lim_run_batch_from on the same errors."""
+    code = I.toric2d(6)
+    lc = ctx.from_inputs(code)
+    prm = L.params(precision="f32", tick_budget=64)
+    pts = [(lc, 0.0, 48, 0, 2)]
+    g = L.Batch(ctx, pts, prm, e_final=True)
+    buf = torch.zeros(g.nshots * g.words, dtype=torch.int32, device="cuda")
+    g.capture(e0=buf)
+    rng = np.random.default_rng(8)
+    for trial in range(2):
+        bits = (rng.random((g.nshots, code.n)) < 0.08 + 0.04 * trial).astype(np.uint8)
+        host = torch.from_numpy(_pack_rows(bits, g.words).view(np.int32).reshape(-1))
+        buf.copy_(host.cuda())
+        g.replay(5, 0)
+        torch.cuda.synchronize()
+        ref = L.Batch(ctx, pts, prm, e_final=True)
+        ref.run(5, e0=host.cuda())
+        torch.cuda.synchronize()
+        assert np.array_equal(g.records(), ref.records()), trial
+        assert np.array_equal(g.finals(), ref.finals()), trial
+
+
 def test_discrete_machine_on_a_quantum_code(L, ctx):
     prm = L.params(feedback="bit_discrete", precision="f32", tick_budget=60, tau=0, dt_tick=0)
     _batch_vs_oracle(L, ctx, I.toric2d(6), prm, 0.04, 100)
