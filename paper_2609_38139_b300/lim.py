@@ -2,8 +2,8 @@
 
 Argument marshalling only: every step of the inference machine runs in the
 CUDA library ``liblim.so``.  PyTorch provides device memory (workspace, output
-buffers) and streams.  If the library is missing, importing this module fails
-loudly: there is no fallback implementation.
+buffers) and streams.  If the library is missing, the first call into it raises
+LimError: there is no fallback implementation.
 """
 from __future__ import annotations
 
