@@ -139,3 +139,28 @@ def test_adaptive_stopping_rule():
     hi, lo = tot[0], tot[1]
     assert hi["failures"] >= 10 and hi["shots"] < 96 and hi["shots"] % 16 == 0
     assert lo["shots"] == 96 and lo["failures"] < 10
+
+
+def test_strong_shards_cover_every_shot_once():
+    """Strong scaling splits each point's shots into contiguous, disjoint ranges
+    that cover all shot ids, also when shots < ranks or do not divide evenly."""
+    pts = [("c", 0.1, 7, 100, 0), ("c", 0.2, 2, 0, 1), ("c", 0.3, 0, 5, 2)]
+    for world in (1, 2, 3, 4):
+        for i, (_, _, shots, shot0, _) in enumerate(pts):
+            ids = []
+            for r in range(world):
+                _, _, n, s0, _ = D.shard(pts, r, world, "strong")[i]
+                ids.extend(range(s0, s0 + n))
+            assert sorted(ids) == list(range(shot0, shot0 + shots)), (world, i)
+    with pytest.raises(ValueError):
+        D.shard(pts, 0, 2, "diagonal")
+
+
+def test_config_hash_identifies_the_run():
+    pts = _points()
+    h = D.config_hash(pts, {"precision": "f32", "T": 24}, 11)
+    assert h == D.config_hash(pts, {"T": 24, "precision": "f32"}, 11)    # key order irrelevant
+    assert h != D.config_hash(pts, {"precision": "f16", "T": 24}, 11)
+    assert h != D.config_hash(pts, {"precision": "f32", "T": 24}, 12)
+    moved = [pts[0][:3] + (pts[0][3] + 1,) + pts[0][4:]] + pts[1:]
+    assert h != D.config_hash(moved, {"precision": "f32", "T": 24}, 11)
