@@ -51,7 +51,8 @@ extern "C" {
 #define LIM_E_INVAL 1       /* bad argument (null pointer, size, malformed CSR ...)   */
 #define LIM_E_NOMEM 2       /* host or device allocation failed, workspace too small  */
 #define LIM_E_CUDA 3        /* a CUDA runtime call failed                             */
-#define LIM_E_TIMEOUT 4     /* a device-side bounded loop gave up                     */
+#define LIM_E_TIMEOUT 4     /* reserved for a device-side bounded wait that gives up;  */
+                            /* no call returns it: no kernel waits on another block   */
 #define LIM_E_NOT_CSS 5     /* H_Z H_X^T != 0                                         */
 #define LIM_E_UNSUPPORTED 6 /* valid request outside what the library supports       */
 
@@ -276,8 +277,8 @@ int lim_run_batch_host(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const 
 
 /* lim_run_batch without any device allocation, for callers that cannot call
  * cudaMalloc while they run (a real-time loop that must not block on the
- * allocator, memory owned by another framework's pool, launches being recorded
- * into a CUDA graph).  The paper has no counterpart: this is an interface
+ * allocator, which may synchronise the device; memory owned by another
+ * framework's pool).  The paper has no counterpart: this is an interface
  * convenience.  The workspace is a 64 MiB array inside the library, held by
  * every device that loads the library until the process exits; batches whose
  * lim_workspace_size() exceeds 64 MiB are refused with LIM_E_NOMEM (use

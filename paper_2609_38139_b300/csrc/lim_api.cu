@@ -1033,10 +1033,9 @@ int lim_readout(const lim_code *code, const lim_params *prm, uint32_t nstates, c
 // Batch runs without any device allocation.
 //
 // Some callers cannot call cudaMalloc while they run trajectories: a real-time
-// controller that must not block (cudaMalloc may synchronise the device), a
-// process whose device memory is owned by another framework's pool, or code
-// that records its launches into a CUDA graph (cudaMalloc is not allowed during
-// stream capture).  lim_run_batch_static serves them with a workspace that lives
+// controller that must not block (cudaMalloc may synchronise the device), or a
+// process whose device memory is owned by another framework's pool.
+// lim_run_batch_static serves them with a workspace that lives
 // in this file-scope array instead of a caller-provided buffer.  The array is
 // allocated when the library is loaded and every device that loads it holds it
 // until the process exits.
@@ -1044,7 +1043,7 @@ int lim_readout(const lim_code *code, const lim_params *prm, uint32_t nstates, c
 namespace {
 
 constexpr size_t kStaticWorkspaceBytes = size_t(64) << 20;  // 64 MiB
-__device__ __align__(256) uint8_t g_static_workspace[kStaticWorkspaceBytes];
+static __device__ __align__(256) uint8_t g_static_workspace[kStaticWorkspaceBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
@@ -1080,31 +1079,20 @@ extern "C" int lim_run_batch_static(lim_ctx *ctx, const lim_point *pts, uint32_t
   return guarded([&] {
     if (!ctx || !tally) return bad(LIM_E_INVAL, "null context or tally");
     if (ctx->device < 0) return bad(LIM_E_INVAL, "host-only context cannot run kernels");
-    DevParams dp;
-    int st = derive(prm, dp);
+    if (prm && prm->variant == LIM_VARIANT_PLAIN)
+      return bad(LIM_E_UNSUPPORTED, "the plain baseline path needs a caller workspace");
+    size_t need = 0;
+    int st = lim_workspace_size(ctx, pts, npts, prm, &need);
     if (st) return st;
-    Plan pl;
-    st = make_plan(ctx, pts, npts, prm, dp, pl);
-    if (st) return st;
-    if (pl.plain) return bad(LIM_E_UNSUPPORTED, "the plain baseline path needs a caller workspace");
-    if (pl.workspace > kStaticWorkspaceBytes)
+    if (need > kStaticWorkspaceBytes)
       return bad(LIM_E_NOMEM, "this batch needs more workspace than the 64 MiB static array; "
                               "use lim_run_batch with a caller buffer");
     void *ws = nullptr;
     st = static_workspace(ctx->device, &ws);
     if (st) return st;
-    LaunchArgs a;
-    fill_args(pl, pts, npts, prm, dp, seed, ws, a);
-    a.rec = rec;
-    a.e_final = e_final;
-    if (e_final) lim_final_words(pts, npts, &a.e_final_words);
-    a.tally = tally;
-    cudaStream_t s = (cudaStream_t)stream;
-    // the queue counter must start at zero; the rest of the array is scratch
-    cudaError_t err = cudaMemsetAsync(ws, 0, 256, s);
-    if (err == cudaSuccess) err = cudaMemsetAsync(tally, 0, sizeof(lim_tally) * npts, s);
-    if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync");
-    if (a.total_items == 0) return LIM_OK;
-    return launch_batch(a, pl.warp, pl.grid, pl.block, pl.smem, stream);
+    // the batch itself, as lim_run_batch runs it (it clears the queue counter
+    // and the tally; the rest of the array is scratch)
+    return run_batch(ctx, pts, npts, prm, seed, nullptr, ws, kStaticWorkspaceBytes, rec, e_final,
+                     tally, stream);
   });
 }

@@ -443,24 +443,30 @@ def autotune(ctx: Context, points, prm: Params, sample_shots: int = 4, sample_ti
     return best, rate.value
 
 
-def run_batch_static(ctx: Context, points, prm: Params, seed: int, stream=None):
+def run_batch_static(ctx: Context, points, prm: Params, seed: int, stream=None, e_final: bool = False):
     """``run_batch`` through ``lim_run_batch_static``: the library's own 64 MiB
     device workspace instead of a buffer from the caller, for callers that cannot
     allocate device memory while they run.  Output buffers still come from the
-    caller (here: torch).  Returns (tallies, records) on the host."""
+    caller (here: torch).  Returns (tallies, records[, finals]) on the host."""
     import torch
     pts = _points(points)
     nshots = sum(int(p[2]) for p in points)
     dev = torch.device("cuda", ctx.device)
     tally = torch.zeros(len(points) * TALLY_DTYPE.itemsize, dtype=torch.uint8, device=dev)
     rec = torch.empty(max(nshots, 1) * RECORD_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    words = final_words(points) if e_final else 0
+    fin = torch.empty(max(nshots * words, 1), dtype=torch.int32, device=dev) if e_final else None
     check(lib().lim_run_batch_static(ctx.handle, pts, len(points), ctypes.byref(prm), int(seed),
-                                     rec.data_ptr(), None, tally.data_ptr(), _stream_ptr(stream)),
+                                     rec.data_ptr(), None if fin is None else fin.data_ptr(),
+                                     tally.data_ptr(), _stream_ptr(stream)),
           "lim_run_batch_static")
     torch.cuda.synchronize(ctx.device)
     t = np.frombuffer(tally.cpu().numpy().tobytes(), dtype=TALLY_DTYPE).copy()
     r = np.frombuffer(rec.cpu().numpy().tobytes()[:nshots * RECORD_DTYPE.itemsize], dtype=RECORD_DTYPE).copy()
-    return t, r
+    if not e_final:
+        return t, r
+    f = fin.cpu().numpy().view(np.uint32)[:nshots * words].reshape(nshots, words).copy()
+    return t, r, f
 
 
 def sample_noise(code: Code, p: float, seed: int, point_id: int, shot0: int, nshots: int, stream=None):

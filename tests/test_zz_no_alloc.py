@@ -1,12 +1,13 @@
 """lim_run_batch_static: batch runs for callers that cannot allocate device memory.
 
-A real-time control loop, a process whose GPU memory belongs to another
-framework's pool, or code recording launches into a CUDA graph cannot call
-cudaMalloc while it runs trajectories.  lim_run_batch_static uses a 64 MiB
-workspace built into the library instead of a caller buffer.  These tests
-check, through the C ABI, that it returns exactly what lim_run_batch returns
-(the same shots, bit for bit), twice in a row on the shared array, and that a
-batch too large for the array is refused.  This file is collected last.
+A real-time control loop that must not block on the allocator, or a process
+whose GPU memory belongs to another framework's pool, cannot call cudaMalloc
+while it runs trajectories.  lim_run_batch_static uses a 64 MiB workspace built
+into the library instead of a caller buffer.  These tests check, through the C
+ABI, that it returns exactly what lim_run_batch returns (records, tallies and
+final residuals of the same shots, bit for bit), twice in a row on the shared
+array, and that a batch too large for the array is refused.  This file is
+collected last.
 """
 import numpy as np
 import pytest
@@ -46,10 +47,11 @@ def test_static_workspace_matches_caller_workspace(L):
     assert 1 << 20 < ws <= 64 << 20
     for call, shot0 in enumerate((0, 1000)):  # two calls in a row share the array
         pts, keep = _points(ctx, shot0)
-        tal_ref, rec_ref = L.run_batch(ctx, pts, prm, 17)
-        tal, rec = L.run_batch_static(ctx, pts, prm, 17)
+        tal_ref, rec_ref, fin_ref = L.run_batch(ctx, pts, prm, 17, e_final=True)
+        tal, rec, fin = L.run_batch_static(ctx, pts, prm, 17, e_final=True)
         assert np.array_equal(rec, rec_ref), call
         assert np.array_equal(tal, tal_ref), call
+        assert np.array_equal(fin, fin_ref), call
         assert int(tal["errors"].sum()) == 0 and int(tal["shots"].sum()) == 540
 
 
