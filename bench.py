@@ -5,14 +5,21 @@ Workload (default): the batched 2D toric sweep -- L in {16, 32, 64, 128}, 11
 error rates p in 0.02..0.12, FP32 min-sum, check-centric feedback, one BP
 sweep per tick (dt = tau = 0.1), tick budget 40L, all points mixed in one
 persistent launch.  One step = one lim_run_batch over ``--shots`` fresh shots
-of every point (shot ids advance every step), run to completion.
+of every point (a sample of the configuration's 10^5 per point), run to
+completion.
 
-Prints one JSON line.  ``value`` is shot-ticks per second (ticks executed,
-summed over shots, divided by device time of the steps); msg-updates/s, the
-roofline of the batch kernel, the oracle's CPU rate, the end-to-end rate
-through the public API (records and tallies read back to the host every
-step), the SM clocks seen during the timed region and the number of our
-kernel launches are reported alongside.
+Prints one JSON line.  ``value`` is shot-ticks per second of the main arm
+(ticks executed, summed over shots, divided by the device time of the steps).
+Alongside: msg-updates/s; the roofline of the batch kernel per memory class
+(codes whose messages live in shared memory against the shared-memory copy
+bandwidth measured in this run, codes whose messages live in global memory
+against the measured HBM copy bandwidth) with the measured DRAM traffic;
+``lowprec``: the same shots with 16-bit storage (f16, i16); ``vs_plain``: the
+plain FP32 per-shot path (one launch per tick, host-polled termination) on the
+shots of step 0, with every arm's failures on those shots paired against it;
+the oracle's CPU rate; the end-to-end rate through the public API (host
+buffers, copies inside the timed region); the SM clocks seen during the timed
+regions and the number of our kernel launches.
 
 ``--impl reference`` times the CPU oracle (the plain reference implementation)
 on a bounded sample of the same workload instead.
@@ -57,7 +64,7 @@ def workload(name: str, shots: int, sizes=None, ps=None):
 
 
 def lib_params(L, w, name, prec, variant="auto"):
-    qs = 0.25 if prec == "i8" else 2 ** -6
+    qs = L.default_quant_scale(prec, w["q"])
     return L.params(rule=w.get("rule", "minsum"), feedback=w.get("feedback", "check_move"),
                     precision=prec, quant_scale=qs,
                     q=w["q"], clamp=w["clamp"], tau=w["tau"],
@@ -137,6 +144,11 @@ def peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def _default_quant_scale(prec: str, q: float) -> float:
+    from paper_2609_38139_b300 import lim
+    return lim.default_quant_scale(prec, q)
+
+
 def cpu_baseline(name: str, prec: str, seconds: float = 15.0, threads: int = 0, rule: str = "",
                  sweeps: int = 0, feedback: str = ""):
     """The oracle timed on this host's cores on a bounded sample of the workload:
@@ -173,7 +185,7 @@ def cpu_baseline(name: str, prec: str, seconds: float = 15.0, threads: int = 0, 
                 c, oc = codes[(d["family"], d["size"])]
                 op = O.params(precision=prec if prec in ("f32", "f16", "bf16", "i16", "i8") else "f64",
                               rule=w.get("rule", "minsum"), feedback=w.get("feedback", "check_move"),
-                              quant_scale=0.25 if prec == "i8" else 2 ** -6,
+                              quant_scale=_default_quant_scale(prec, w["q"]),
                               q=w["q"], clamp=w["clamp"], tau=w["tau"],
                               dt_tick=w["dt_tick"], sweeps_per_tick=w["K"], tick_budget=d["T"])
                 futs.append((c, ex.submit(O.run_shots, oc, op, d["p"], 0, d["point_id"], rnd, 1)))
@@ -191,10 +203,12 @@ def cpu_baseline(name: str, prec: str, seconds: float = 15.0, threads: int = 0, 
 
 
 def arm_config(args, w, npoints: int) -> dict:
-    """The workload as both arms describe it in their JSON lines."""
+    """The workload as both arms describe it in their JSON lines (identical for
+    both; what each arm actually timed is in its ``sample`` key)."""
     return {"workload": args.workload, "codes": f"{w['family']} sizes {w['sizes']}",
-            "points": npoints, "shots_per_point_per_step": args.shots,
-            "shots_per_step": args.shots * npoints,
+            "points": npoints,
+            "shots_per_point": f"timed on samples of fresh shot ids; the configuration has "
+                               f"{w['shots']} per point",
             "rule": w.get("rule", "minsum"), "feedback": w.get("feedback", "check_move"),
             "tau": w["tau"], "dt_tick": w["dt_tick"], "sweeps_per_tick": w.get("K", 1),
             "tick_budget": w["budget"], "variant": args.variant,
@@ -232,6 +246,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": dict(arm_config(args, w, npts), parallelism="host threads",
                            launch_shape="oracle, shots of every point in turn"),
+            "sample": f"each step: {last['sample']}",
             "cpu_baseline": {"value": val, "unit": "shot-ticks/s", "cores": last["cores"],
                              "kind": "oracle", "sample": last["sample"]},
             "e2e": {"value": val, "unit": "shot-ticks/s", "h2d_bytes_per_step": 0,
@@ -248,6 +263,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="toric2d_sweep")
     ap.add_argument("--precision", default="f32")
+    ap.add_argument("--lowprec", default="auto",
+                    help="comma list of further storage precisions timed on the same shots "
+                         "(auto: f16,i16 when the main arm is f32; none: skip)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain per-tick FP32 path")
     ap.add_argument("--variant", default="auto")
     ap.add_argument("--shots", type=int, default=0,
                     help="shots per point per step (default: the workload's bench_shots, else 32)")
@@ -303,15 +322,23 @@ def main():
         key = (d["family"], d["size"])
         if key not in codes:
             codes[key] = ctx.from_inputs(I.make_code(*key))
-    prm = lib_params(L, w, args.workload, args.precision, args.variant)
-    prm.block_threads = args.block_threads
-    prm.blocks_per_sm = args.blocks_per_sm
-    prm.profile = 1 if args.phases else 0
-    prm.smem_cap = args.smem_cap
-    # weak scaling: every rank runs its own disjoint shot ids of every point
-    def step_points(step):
+
+    def make_params(prec, variant=None):
+        prm = lib_params(L, w, args.workload, prec, variant or args.variant)
+        prm.block_threads = args.block_threads
+        prm.blocks_per_sm = args.blocks_per_sm
+        prm.profile = 1 if args.phases else 0
+        prm.smem_cap = args.smem_cap
+        return prm
+
+    prm = make_params(args.precision)
+
+    # weak scaling: every rank runs its own disjoint shot ids of every point;
+    # every arm below runs the same shot ids (step i of an arm = step i of another)
+    def step_points(step, shots=None):
+        n = shots or args.shots
         base = (step * world + rank) * args.shots
-        return [(codes[(d["family"], d["size"])], d["p"], d["shots"], base, d["point_id"], d["T"])
+        return [(codes[(d["family"], d["size"])], d["p"], n, base, d["point_id"], d["T"])
                 for d in pts]
 
     tuned = None
@@ -322,63 +349,107 @@ def main():
         tuned = {"variant": int(prm.variant), "block_threads": int(prm.block_threads),
                  "blocks_per_sm": int(prm.blocks_per_sm), "smem_cap": int(prm.smem_cap),
                  "sample_rate": rate}
-    batch = L.Batch(ctx, step_points(0), prm, records=True)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 126 MB L2
-    step_id = [0]
 
-    def run_step(timed_events=None):
-        batch.points = step_points(step_id[0])
-        batch.pts = L._points(batch.points)
-        step_id[0] += 1
-        flush.fill_(step_id[0] & 0xFF)  # evict L2 between steps (outside the timed window)
-        if timed_events:
-            timed_events[0].record(stream)
-        batch.run(0, stream)
-        if timed_events:
-            timed_events[1].record(stream)
+    def timed_arm(arm_prm):
+        """W untimed and K timed steps of one storage precision: device times of the
+        steps (CUDA events on the launching stream), their tallies, and the step-0
+        records (for the paired comparisons)."""
+        batch = L.Batch(ctx, step_points(0), arm_prm, records=True)
 
-    for _ in range(args.warmup):
-        run_step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clocks = Clocks(local)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    tallies = []
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        run_step(evs[i])
-        tallies.append(batch.tally.clone())
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-    ms = [a.elapsed_time(b) for a, b in evs]
-    tot_ms = sum(ms)
-    ticks = upd = shots = fails = 0
-    phase = np.zeros(len(L.PHASES))
-    for t in tallies:
-        arr = np.frombuffer(t.cpu().numpy().tobytes(), dtype=L.TALLY_DTYPE)
-        phase += arr["phase_cycles"].sum(axis=0)
-        ticks += int(arr["ticks"].sum())
-        upd += int(arr["msg_updates"].sum())
-        shots += int(arr["shots"].sum())
-        fails += int(arr["failures"].sum())
-        assert int(arr["errors"].sum()) == 0, "device-side error counter set"
-    if dist:
-        t = torch.tensor([tot_ms, ticks, upd, shots], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        tot_ms = float(mx[0])
-        ticks, upd, shots = int(t[1]), int(t[2]), int(t[3])
-    value = ticks / (tot_ms / 1000.0)
-    upd_rate = upd / (tot_ms / 1000.0)
-    bpm = L.MSG_BYTES[args.precision]
+        def run_step(step, timed_events=None):
+            batch.points = step_points(step)
+            batch.pts = L._points(batch.points)
+            flush.fill_(step & 0xFF)  # evict L2 between steps (outside the timed window)
+            if timed_events:
+                timed_events[0].record(stream)
+            batch.run(0, stream)
+            if timed_events:
+                timed_events[1].record(stream)
+
+        for i in range(args.warmup):
+            run_step(args.steps + i)  # warm-up on shot ids the timed steps do not use
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        tallies, rec0 = [], None
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            run_step(i, evs[i])
+            tallies.append(batch.tally.clone())
+            if i == 0:
+                rec0 = batch.rec.clone()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        arrs = [np.frombuffer(t.cpu().numpy().tobytes(), dtype=L.TALLY_DTYPE) for t in tallies]
+        for a in arrs:
+            assert int(a["errors"].sum()) == 0, "device-side error counter set"
+        recs = np.frombuffer(rec0.cpu().numpy().tobytes()[:batch.nshots * L.RECORD_DTYPE.itemsize],
+                             dtype=L.RECORD_DTYPE).copy()
+        return {"ms": sum(ms), "tallies": arrs, "rec0": recs}
+
+    def reduce_arm(arm):
+        """Whole-job totals of an arm: max of the ranks' device times, sums of work."""
+        tot_ms = arm["ms"]
+        ticks = sum(int(a["ticks"].sum()) for a in arm["tallies"])
+        upd = sum(int(a["msg_updates"].sum()) for a in arm["tallies"])
+        shots = sum(int(a["shots"].sum()) for a in arm["tallies"])
+        fails = sum(int(a["failures"].sum()) for a in arm["tallies"])
+        if dist:
+            t = torch.tensor([tot_ms, ticks, upd, shots, fails], dtype=torch.float64, device="cuda")
+            mx = t.clone()
+            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            tot_ms = float(mx[0])
+            ticks, upd, shots, fails = (int(x) for x in t[1:].tolist())
+        return tot_ms, ticks, upd, shots, fails
+
     hbm, hbm_src = peak_hbm()
-    achieved = upd * 2 * bpm / (tot_ms / 1000.0) / 1e9 / world
+    smem_copy_gbs, smem_load_gbs = L.smem_bandwidth(ctx)
+    _, msg_smem = L.plan_describe(ctx, step_points(0), prm)
+
+    def roofline(arm, prec, tot_ms):
+        """Roofline of the batch kernel per memory class: codes whose messages live
+        in shared memory against the measured shared-memory copy bandwidth, codes
+        whose messages live in global memory against the measured HBM copy
+        bandwidth; the class whose bytes take longer at its peak bounds the launch.
+        Algorithmic bytes: 2 x b per message update (read the old message, write the
+        new one)."""
+        bpm = L.MSG_BYTES[prec]
+        _, sm = L.plan_describe(ctx, step_points(0), make_params(prec))
+        upd_pt = np.sum([a["msg_updates"] for a in arm["tallies"]], axis=0).astype(np.float64)
+        b_smem = float(upd_pt[sm].sum()) * 2 * bpm / world
+        b_glob = float(upd_pt[~sm].sum()) * 2 * bpm / world
+        sec = tot_ms / 1000.0
+        cls = {"smem": {"bytes_per_launch": b_smem / args.steps, "achieved_gbs": b_smem / sec / 1e9,
+                        "peak_gbs": smem_copy_gbs, "frac": b_smem / sec / 1e9 / smem_copy_gbs,
+                        "peak_source": "measured (lim_smem_bandwidth copy, this run)"},
+               "global": {"bytes_per_launch": b_glob / args.steps, "achieved_gbs": b_glob / sec / 1e9,
+                          "peak_gbs": hbm, "frac": b_glob / sec / 1e9 / hbm,
+                          "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}}
+        dom = "smem" if b_smem / smem_copy_gbs > b_glob / hbm else "global"
+        c = cls[dom]
+        traffic = measured_traffic(args.workload, prec, (b_smem + b_glob) / args.steps)
+        out = {"bound": "smem" if dom == "smem" else "hbm", "achieved": c["achieved_gbs"],
+               "peak": c["peak_gbs"], "unit": "GB/s", "frac": c["frac"], "traffic": traffic,
+               "kernel": "batch_kernel (persistent)",
+               "algorithmic_bytes": "2 x msg bytes per message update (read old, write new), "
+                                    "of the codes in the bounding memory class",
+               "peak_source": c["peak_source"], "classes": cls}
+        if traffic is not None:
+            out["dram_achieved_gbs"] = traffic * args.steps / sec / 1e9
+            out["dram_frac"] = out["dram_achieved_gbs"] / hbm
+        return out
+
+    clocks = Clocks(local)
+    main_arm = timed_arm(prm)
+    tot_ms, ticks, upd, shots, fails = reduce_arm(main_arm)
+    value = ticks / (tot_ms / 1000.0)
     line = {"metric": METRIC, "value": value, "unit": "shot-ticks/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -386,20 +457,74 @@ def main():
             "config": dict(arm_config(args, w, len(pts)),
                            parallelism=f"replicas x{world}, disjoint shot ids",
                            launch_shape=tuned or "library default"),
-            "msg_updates_per_s": upd_rate,
+            "sample": f"{args.shots} fresh shot ids of every point per step "
+                      f"({args.shots * len(pts)} shots per launch, one launch per step)",
+            "msg_updates_per_s": upd / (tot_ms / 1000.0),
             "ler_sample": fails / max(1, shots),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm,
-                         "traffic": measured_traffic(args.workload, args.precision,
-                                                     upd * 2 * bpm / args.steps / world),
-                         "algorithmic_bytes_per_launch": upd * 2 * bpm / args.steps / world,
-                         "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)",
-                         "kernel": "batch_kernel (persistent)",
-                         "algorithmic_bytes": "2 x msg bytes per message update (read old, write new)"},
-            "clocks": clk, "gpu_launches": args.steps}
-    if args.phases and phase.sum() > 0:
-        line["phase_share"] = {n: round(float(v / phase.sum()), 4) for n, v in zip(L.PHASES, phase)}
-        line["phase_cycles_per_tick"] = float(phase.sum() / max(1, ticks))
+            "roofline": roofline(main_arm, args.precision, tot_ms),
+            "smem_peak": {"copy_gbs": smem_copy_gbs, "load_gbs": smem_load_gbs,
+                          "how": "lim_smem_bandwidth: two 1024-thread blocks per SM moving 16-byte "
+                                 "words in shared memory, best of three launches"},
+            "gpu_launches": args.steps}
+    if args.phases:
+        phase = np.sum([a["phase_cycles"].sum(axis=0) for a in main_arm["tallies"]], axis=0)
+        if phase.sum() > 0:
+            line["phase_share"] = {n: round(float(v / phase.sum()), 4) for n, v in zip(L.PHASES, phase)}
+            line["phase_cycles_per_tick"] = float(phase.sum() / max(1, ticks))
+
+    # the same shots in reduced-precision storage
+    low = [x for x in args.lowprec.split(",") if x] if args.lowprec != "auto" else \
+        (["f16", "i16"] if args.precision == "f32" else [])
+    if args.lowprec == "none":
+        low = []
+    arms = {args.precision: main_arm}
+    lowprec = {}
+    for lp in low:
+        arm = timed_arm(make_params(lp))
+        arms[lp] = arm
+        a_ms, a_ticks, a_upd, a_shots, a_fails = reduce_arm(arm)
+        lowprec[lp] = {"value": a_ticks / (a_ms / 1000.0), "unit": "shot-ticks/s",
+                       "ms_per_step": a_ms / args.steps,
+                       "msg_updates_per_s": a_upd / (a_ms / 1000.0),
+                       "ler_sample": a_fails / max(1, a_shots),
+                       "roofline": roofline(arm, lp, a_ms)}
+    if lowprec:
+        line["lowprec"] = lowprec
+    clk = clocks.stop()
+    line["clocks"] = clk
+    line["gpu_launches"] = args.steps * (1 + len(low))
+
+    # the plain FP32 per-shot path (one launch per tick, host-polled termination)
+    # on the shots of step 0, and every batched arm's failures on those shots
+    if not args.no_plain and world == 1:
+        plain_prm = make_params("f32", variant="plain")
+        pb = L.Batch(ctx, step_points(0), plain_prm, records=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pb.run(0, stream)
+        torch.cuda.synchronize()
+        p_dt = time.perf_counter() - t0
+        p_tal = pb.tallies()
+        p_rec = pb.records()
+        vs = {"plain_f32": {"value": int(p_tal["ticks"].sum()) / p_dt, "unit": "shot-ticks/s",
+                            "shots": int(p_tal["shots"].sum()),
+                            "failures": int(p_tal["failures"].sum()),
+                            "ler": float(p_tal["failures"].sum() / max(1, p_tal["shots"].sum())),
+                            "timing": "wall clock of one lim_run_batch (the plain path polls the "
+                                      "host every tick), same shot ids as every arm's step 0"}}
+        for prec, arm in arms.items():
+            r0 = arm["rec0"]
+            b = int(np.sum((r0["failed"] == 1) & (p_rec["failed"] == 0)))
+            c = int(np.sum((r0["failed"] == 0) & (p_rec["failed"] == 1)))
+            rate = value if prec == args.precision else lowprec[prec]["value"]
+            vs[f"batched_{prec}"] = {
+                "failures_same_shots": int(r0["failed"].sum()),
+                "paired_vs_plain": {"gpu_only": b, "plain_only": c,
+                                    "within_3_sigma": bool(abs(b - c) <= 3 * np.sqrt(b + c) + 1)},
+                "identical_records": bool(np.array_equal(r0, p_rec)),
+                "speedup_shot_ticks": rate / vs["plain_f32"]["value"]}
+        line["vs_plain"] = vs
+
     # end to end through the public API: lim_run_batch_host, one blocking call per
     # step with host buffers -- the step's initial errors are copied in from
     # page-locked host memory, the records, final residuals and tallies are
@@ -410,7 +535,7 @@ def main():
         hb = L.HostBatch(ctx, [pt[:3] + (0,) + tuple(pt[4:]) for pt in step_points(0)], prm)
         e2e_steps = []
         for i in range(args.steps):
-            off = ((step_id[0] + i) * world + rank) * args.shots
+            off = (i * world + rank) * args.shots
             buf = torch.zeros(hb.nshots * hb.words, dtype=torch.int32, pin_memory=True)
             view = buf.view(hb.nshots, hb.words)
             row = 0
@@ -430,7 +555,6 @@ def main():
             hb.run(0, e0=buf, stream=stream)
             e_ticks += int(hb.tallies()["ticks"].sum())
         e_dt = time.perf_counter() - t0
-        step_id[0] += args.steps
         if world > 1:
             tt = torch.tensor([e_dt], dtype=torch.float64, device=torch.device("cuda", local))
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -441,7 +565,6 @@ def main():
                        "note": "lim_run_batch_host per step: initial errors of the step's shots "
                                "copied in from page-locked host memory, records, final residuals "
                                "and tallies copied back, inside the timed region"}
-        line["gpu_launches"] = args.steps
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.precision, args.cpu_seconds,
                                             rule=args.rule, sweeps=args.sweeps_per_tick, feedback=args.feedback)

@@ -323,6 +323,22 @@ int lim_graph_destroy(lim_graph *graph);
 int lim_autotune(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
                  uint32_t sample_shots, int32_t sample_ticks, lim_params *best, double *rate_out);
 
+/* The launch plan lim_run_batch uses for these points and params (host only,
+ * for reporting): shape (nullable, 4 ints) = {variant (LIM_VARIANT_CTA, _WARP or
+ * _PLAIN), grid, threads per block, dynamic shared memory per block in bytes};
+ * msg_smem (nullable, npts ints) = 1 where the point's code keeps its messages
+ * in shared memory, 0 where they stream from the workspace in global memory. */
+int lim_plan_describe(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+                      int32_t *shape, int32_t *msg_smem);
+
+/* Measured shared-memory bandwidth of the context's device, the roofline of the
+ * codes whose messages live in shared memory: every thread of two 1024-thread
+ * blocks per SM moves 16-byte words between two shared arrays (copy_gbs: bytes
+ * read plus bytes written per second) or only reads them (load_gbs); best of
+ * three timed launches after a warm-up.  Synchronises the device; allocates
+ * nothing.  Either output may be NULL. */
+int lim_smem_bandwidth(lim_ctx *ctx, double *copy_gbs, double *load_gbs);
+
 /* Words per shot of lim_run_batch's e_final rows for this point list. */
 int lim_final_words(const lim_point *pts, uint32_t npts, int32_t *words);
 
@@ -330,11 +346,31 @@ int lim_final_words(const lim_point *pts, uint32_t npts, int32_t *words);
  * feedback of tick t (t = 0 is the initial state), e and s as bit words:
  *   e_hist [(max_ticks+1) * ceil(n/32)], s_hist [(max_ticks+1) * ceil(m/32)]
  * (device; rows after the end repeat the final state); rec (device) the shot's
- * record.  Workspace as for lim_run_batch with one point of one shot. */
+ * record.
+ *   l_hist  device, nullable, [(max_ticks+1) * n] floats: row t (t >= 1) holds
+ *           the read-out L_v = pi_v + sum_c m_{c->v} of tick t (Eq. 3), taken
+ *           before that tick's feedback, in the actual gauge frame; LLR units in
+ *           the floating modes, integer steps in the integer modes.  Row 0 and
+ *           rows after the shot's last tick are not written.
+ *   forced_moves  host, nullable: nforced triples (tick, check, qubit) with
+ *           ticks >= 1 in ascending order -- e.g. the move log of an oracle run.
+ *           When given, the clocks, Evidence and LocalMove of Algorithm 1 are
+ *           replaced by these moves: at tick t the listed qubits are flipped in
+ *           order (and gauge-switched when gauge_on_move is set); read-out,
+ *           syndrome update, termination and the BP sweeps are the machine's
+ *           own.  This runs a trajectory under decisions taken elsewhere, so that
+ *           its messages can be compared with another arithmetic's under
+ *           identical decisions.  Check-centric rules only (LIM_E_UNSUPPORTED for
+ *           the bit-centric rule); the check entry is not used.  The list is
+ *           copied into the workspace on the stream: keep it unchanged until the
+ *           stream passes the call.
+ * workspace (device) >= lim_trace_workspace_size() bytes. */
+int lim_trace_workspace_size(lim_ctx *ctx, const lim_code *code, const lim_params *prm,
+                             int32_t nforced, size_t *bytes);
 int lim_trace(lim_ctx *ctx, const lim_code *code, const lim_params *prm, double p, uint64_t seed,
-              uint32_t point_id, uint32_t shot, int32_t max_ticks, void *workspace,
-              size_t workspace_bytes, uint32_t *e_hist, uint32_t *s_hist, lim_shot_record *rec,
-              void *stream);
+              uint32_t point_id, uint32_t shot, int32_t max_ticks, const int32_t *forced_moves,
+              int32_t nforced, void *workspace, size_t workspace_bytes, uint32_t *e_hist,
+              uint32_t *s_hist, float *l_hist, lim_shot_record *rec, void *stream);
 
 /* BP sweeps on fixed states (Eq. 1-2 with relaxation and clamp, Jacobi: both
  * families from the previous iterate), for message-accuracy and decision-flip

@@ -66,7 +66,8 @@ class Trace(ctypes.Structure):
                 ("s_hist", ctypes.c_void_p), ("move_cap", ctypes.c_int32),
                 ("moves", ctypes.c_void_p), ("n_moves", ctypes.c_int32),
                 ("l_hist", ctypes.c_void_p), ("cv_final", ctypes.c_void_p),
-                ("vc_final", ctypes.c_void_p), ("pi_final", ctypes.c_void_p)]
+                ("vc_final", ctypes.c_void_p), ("pi_final", ctypes.c_void_p),
+                ("e_final", ctypes.c_void_p)]
 
 
 class Derived(ctypes.Structure):
@@ -219,11 +220,12 @@ def run_shot(code: OracleCode, prm: Params, p: float, seed: int, point: int, sho
         out["cv"] = np.zeros(max(code.E, 1))
         out["vc"] = np.zeros(max(code.E, 1))
         out["pi"] = np.zeros(code.n)
+        out["e_final"] = np.zeros(code.n, dtype=np.uint8)
         if want_l:
             out["l_hist"] = np.zeros((T + 1, code.n))
         tr = Trace(T, _ptr(out["e_hist"]), _ptr(out["s_hist"]), move_cap, _ptr(out["moves"]), 0,
                    _ptr(out["l_hist"]) if want_l else None, _ptr(out["cv"]), _ptr(out["vc"]),
-                   _ptr(out["pi"]))
+                   _ptr(out["pi"]), _ptr(out["e_final"]))
     trp = ctypes.byref(tr) if tr is not None else None
     if e0a is None:
         st = lib().or_run_shot(ctypes.byref(code.struct), ctypes.byref(prm), p, seed, point, shot,

@@ -707,6 +707,7 @@ static int run(const or_code *code, const or_params *prm, double p, const uint8_
     if (tr->cv_final) memcpy(tr->cv_final, cv, (size_t)g.E * sizeof(double));
     if (tr->vc_final) memcpy(tr->vc_final, vc, (size_t)g.E * sizeof(double));
     if (tr->pi_final) memcpy(tr->pi_final, pi, (size_t)n * sizeof(double));
+    if (tr->e_final) memcpy(tr->e_final, e, (size_t)n);
   }
   /* Decoding criteria (1)-(2): non-convergence is a failure; otherwise the
    * residual e (= e_0 + correction, H_X e = 0) fails iff it anticommutes with

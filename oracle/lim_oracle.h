@@ -115,6 +115,7 @@ typedef struct {
   double *cv_final;      /* [E] check->qubit messages at the end (as stored)     */
   double *vc_final;      /* [E] qubit->check messages at the end                 */
   double *pi_final;      /* [n] priors at the end                                 */
+  uint8_t *e_final;      /* [n] the error at the end (e_0 plus every flip)        */
 } or_trace;
 
 /* Philox4x32-10 and Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11). */

@@ -576,6 +576,34 @@ int lim_workspace_size(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const 
   });
 }
 
+int lim_plan_describe(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
+                      int32_t *shape, int32_t *msg_smem) {
+  return guarded([&] {
+    DevParams dp;
+    int st = derive(prm, dp);
+    if (st) return st;
+    Plan pl;
+    st = make_plan(ctx, pts, npts, prm, dp, pl);
+    if (st) return st;
+    if (shape) {
+      shape[0] = pl.plain ? LIM_VARIANT_PLAIN : (pl.warp ? LIM_VARIANT_WARP : LIM_VARIANT_CTA);
+      shape[1] = pl.grid;
+      shape[2] = pl.block;
+      shape[3] = (int32_t)pl.smem;
+    }
+    if (msg_smem)
+      for (uint32_t i = 0; i < npts; i++)
+        msg_smem[i] = pl.plain ? 0 : pl.msg_smem[pl.code_of_point[i]];
+    return LIM_OK;
+  });
+}
+
+int lim_smem_bandwidth(lim_ctx *ctx, double *copy_gbs, double *load_gbs) {
+  if (!ctx) return bad(LIM_E_INVAL, "null context");
+  if (ctx->device < 0) return bad(LIM_E_INVAL, "host-only context cannot run kernels");
+  return probe_smem_bandwidth(ctx->device, ctx->num_sms, copy_gbs, load_gbs);
+}
+
 int lim_final_words(const lim_point *pts, uint32_t npts, int32_t *words) {
   if (!pts || !words) return bad(LIM_E_INVAL, "null argument");
   int32_t w = 0;
@@ -940,15 +968,38 @@ int lim_autotune(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_pa
   });
 }
 
+int lim_trace_workspace_size(lim_ctx *ctx, const lim_code *code, const lim_params *prm,
+                             int32_t nforced, size_t *bytes) {
+  return guarded([&] {
+    if (!code || !prm || !bytes || nforced < 0) return bad(LIM_E_INVAL, "bad argument");
+    lim_params one = *prm;
+    if (one.variant == LIM_VARIANT_PLAIN) one.variant = LIM_VARIANT_CTA;
+    lim_point pt = {code, 0.0, 1, 0, 0, 0};
+    size_t ws = 0;
+    int st = lim_workspace_size(ctx, &pt, 1, &one, &ws);
+    if (st) return st;
+    *bytes = a256(ws) + a256((size_t)nforced * 3 * sizeof(int32_t));
+    return LIM_OK;
+  });
+}
+
 int lim_trace(lim_ctx *ctx, const lim_code *code, const lim_params *prm, double p, uint64_t seed,
-              uint32_t point_id, uint32_t shot, int32_t max_ticks, void *workspace,
-              size_t workspace_bytes, uint32_t *e_hist, uint32_t *s_hist, lim_shot_record *rec,
-              void *stream) {
+              uint32_t point_id, uint32_t shot, int32_t max_ticks, const int32_t *forced_moves,
+              int32_t nforced, void *workspace, size_t workspace_bytes, uint32_t *e_hist,
+              uint32_t *s_hist, float *l_hist, lim_shot_record *rec, void *stream) {
   return guarded([&] {
     if (!code || !e_hist || !s_hist || !workspace || max_ticks < 0) return bad(LIM_E_INVAL, "bad argument");
+    if (nforced < 0 || (nforced > 0 && !forced_moves)) return bad(LIM_E_INVAL, "bad forced moves");
     DevParams dp;
     int st = derive(prm, dp);
     if (st) return st;
+    if (forced_moves && dp.feedback != LIM_FB_CHECK_MOVE)
+      return bad(LIM_E_UNSUPPORTED, "forced moves replay the check-centric rules only");
+    for (int32_t i = 0; i < nforced; i++) {
+      const int32_t t = forced_moves[3 * i], v = forced_moves[3 * i + 2];
+      if (t < 1 || (i > 0 && t < forced_moves[3 * (i - 1)]) || v < 0 || v >= code->dev.n)
+        return bad(LIM_E_INVAL, "forced moves: ticks must be >= 1 and ascending, qubits in [0, n)");
+    }
     lim_point pt = {code, p, 1, shot, point_id, 0};
     if (pt.code->dev.m == 0) return bad(LIM_E_INVAL, "empty code");
     lim_params one = *prm;
@@ -956,17 +1007,30 @@ int lim_trace(lim_ctx *ctx, const lim_code *code, const lim_params *prm, double 
     Plan pl;
     st = make_plan(ctx, &pt, 1, &one, dp, pl);
     if (st) return st;
-    if (workspace_bytes < pl.workspace) return bad(LIM_E_NOMEM, "workspace too small");
+    const size_t forced_off = a256(pl.workspace);
+    const size_t need = forced_off + a256((size_t)nforced * 3 * sizeof(int32_t));
+    if (workspace_bytes < need) return bad(LIM_E_NOMEM, "workspace too small (lim_trace_workspace_size)");
     LaunchArgs a;
     fill_args(pl, &pt, 1, &one, dp, seed, workspace, a);
     a.rec = rec;
     a.tally = (lim_tally *)((uint8_t *)workspace + 256);
     a.trace_e = e_hist;
     a.trace_s = s_hist;
+    a.trace_l = l_hist;
     a.trace_ticks = std::min(max_ticks, a.pts[0].T);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t err = cudaMemsetAsync(workspace, 0, kWsHeader, s);
     if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync");
+    if (forced_moves) {
+      int32_t *dst = reinterpret_cast<int32_t *>((uint8_t *)workspace + forced_off);
+      if (nforced > 0) {
+        err = cudaMemcpyAsync(dst, forced_moves, (size_t)nforced * 3 * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, s);
+        if (err != cudaSuccess) return cuda_fail(err, "copy of the forced moves");
+      }
+      a.forced = dst;
+      a.nforced = nforced;
+    }
     // rows beyond the budget are never written by the kernel: clear them
     const int T = a.pts[0].T;
     if (max_ticks > T) {

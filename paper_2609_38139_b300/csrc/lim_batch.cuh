@@ -28,7 +28,7 @@ struct TeamCtl {
   uint32_t logmask; // parities of e with the X-logicals
   int32_t t_clr, converged, ticks, sweeps, vc_sel, done;
   int32_t work[2];  // chunk counters of the dynamically distributed sweep, by tick parity
-  int32_t pad;
+  int32_t forced;   // next replayed move (lim_trace with forced moves)
 };
 static_assert(sizeof(TeamCtl) == 64, "TeamCtl layout");
 
@@ -136,6 +136,21 @@ __device__ __forceinline__ void write_trace(const Team &tm, const LaunchArgs &A,
   for (int w = tm.rank(); w < C.mw; w += tm.size()) A.trace_s[(size_t)row * C.mw + w] = s[w];
 }
 
+// Read-out of every qubit at tick t (Eq. 3) in the actual gauge frame, for the
+// trace: binary32 LLR units in the floating modes, integer steps in the integer
+// modes (exact as float: |L| < 2^24).
+template <class Team, int PREC>
+__device__ __forceinline__ void write_trace_l(const Team &tm, const LaunchArgs &A, const DevCode &C,
+                                              int t, const typename MT<PREC>::T *CV,
+                                              const uint32_t *sg, bool frame) {
+  if (t > A.trace_ticks) return;
+  for (int v = tm.rank(); v < C.n; v += tm.size()) {
+    const auto L = belief<PREC>(C, A.prm, v, CV);
+    const bool neg = frame && ((sg[v >> 5] >> (v & 31)) & 1);
+    A.trace_l[(size_t)t * C.n + v] = (float)(neg ? -L : L);
+  }
+}
+
 // --- init: noise and initial syndrome (Preliminaries), m = 0 (Algorithm 1) ----
 // The initial error is the sampled i.i.d. noise, or row `item` of A.e_init when
 // the caller gives the errors (bits beyond n ignored).
@@ -185,6 +200,7 @@ __device__ void shot_init(const Team &tm, const LaunchArgs &A, const DevPoint &p
     V.ctl->done = 0;
     V.ctl->work[0] = 0;
     V.ctl->work[1] = 0;
+    V.ctl->forced = 0;
   }
   tm.sync();
   // s = H_X e: a warp per syndrome word, lane l computes the parity of check
@@ -299,6 +315,14 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
   int32_t *const work = Team::is_warp ? nullptr : &ctl->work[t & 1];
   if (!Team::is_warp && tm.rank() == 0) ctl->work[(t + 1) & 1] = 0;
   int nc = 0;
+  if (A.trace_l) {  // trace only: every belief of this tick, before any flip
+    write_trace_l<Team, PREC>(tm, A, C, t, CV, V.sg, frame_s0);
+    tm.sync();
+  }
+  // Replay (trace only): the moves of this tick come from the caller's list
+  // instead of the clocks, Evidence and LocalMove; the rest of the tick is the
+  // machine's own (flips, syndrome, sweeps).
+  const bool replay = A.forced != nullptr;
   // --- read-out + feedback (+ the qubit half-sweep of sweep 1, which reads the
   //     same messages and does not depend on the feedback) --------------------
   if (kCheck) {
@@ -311,7 +335,7 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
     const int lane = tm.rank() & 31;
     const int w0 = by_thread ? tm.rank() : tm.rank() >> 5;
     const int ws = by_thread ? tm.size() : tm.size() >> 5;
-    for (int w = w0; w < C.mw; w += ws) {
+    for (int w = replay ? C.mw : w0; w < C.mw; w += ws) {
       uint32_t bits = V.s[w];
       if (!by_thread) bits &= 1u << lane;
       while (bits) {
@@ -397,7 +421,21 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
   }
   tm.sync();
   clk.mark(1);
-  if (kCheck) {
+  if (kCheck && replay) {
+    if (tm.rank() == 0) {
+      int k = ctl->forced, applied = 0;
+      while (k < A.nforced && A.forced[3 * k] < t) k++;  // moves of ticks the shot never ran
+      for (; k < A.nforced && A.forced[3 * k] == t; k++, applied++) {
+        const int v = A.forced[3 * k + 2];
+        flip_bits(C, F, v);
+        if (P.gauge_on_move) V.sg[v >> 5] ^= 1u << (v & 31);
+      }
+      ctl->forced = k;
+      ctl->ncand = applied;
+    }
+    tm.sync();
+    nc = ctl->ncand;  // rewritten only after the next tick's first barrier
+  } else if (kCheck) {
     nc = ctl->ncand;
     if (nc > 0) {
       if (!P.gauge_on_move) {

@@ -82,7 +82,10 @@ struct LaunchArgs {
   lim_tally *tally;        // [npts]
   // trace of one item (lim_trace)
   uint32_t *trace_e, *trace_s;
+  float *trace_l;          // nullable: read-out L_v of every tick, [(trace_ticks+1) * n]
   int32_t trace_ticks;
+  const int32_t *forced;   // nullable: replayed moves (tick, check, qubit), ticks ascending
+  int32_t nforced;
   DevCode codes[LIM_MAX_CODES];
   DevPoint pts[LIM_MAX_POINTS];
 };
@@ -139,5 +142,8 @@ int launch_bp_sweep(const DevCode &c, const DevParams &p, uint32_t nstates, cons
                     void *stream);
 int launch_readout(const DevCode &c, const DevParams &p, uint32_t nstates, const void *cv,
                    float *L, void *stream);
+// Shared-memory bandwidth of the device (lim_probe.cu): copy (read + write bytes)
+// and load-only GB/s over every SM, best of three timed launches.
+int probe_smem_bandwidth(int device, int num_sms, double *copy_gbs, double *load_gbs);
 
 }  // namespace lim

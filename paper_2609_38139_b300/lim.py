@@ -36,8 +36,8 @@ EXPORTS = ["lim_last_error", "lim_version", "lim_ctx_create", "lim_ctx_destroy",
            "lim_code_export", "lim_code_destroy", "lim_sample_noise", "lim_params_check",
            "lim_workspace_size", "lim_run_batch", "lim_run_batch_from", "lim_workspace_size_host",
            "lim_run_batch_host", "lim_run_batch_static", "lim_graph_create", "lim_graph_create_from",
-           "lim_graph_launch", "lim_graph_destroy", "lim_autotune", "lim_final_words",
-           "lim_trace", "lim_bp_sweeps", "lim_readout"]
+           "lim_graph_launch", "lim_graph_destroy", "lim_autotune", "lim_plan_describe", "lim_smem_bandwidth", "lim_final_words",
+           "lim_trace_workspace_size", "lim_trace", "lim_bp_sweeps", "lim_readout"]
 
 
 LIM_MAX_POINTS = 128  # points per lim_run_batch call (include/lim.h)
@@ -124,8 +124,12 @@ def lib() -> ctypes.CDLL:
     L.lim_autotune.argtypes = [vp, vp, u32, ctypes.POINTER(Params), u32, i32, ctypes.POINTER(Params),
                                ctypes.POINTER(ctypes.c_double)]
     L.lim_final_words.argtypes = [vp, u32, ctypes.POINTER(i32)]
-    L.lim_trace.argtypes = [vp, vp, ctypes.POINTER(Params), dbl, u64, u32, u32, i32, vp,
-                            ctypes.c_size_t, vp, vp, vp, vp]
+    L.lim_plan_describe.argtypes = [vp, vp, u32, ctypes.POINTER(Params), vp, vp]
+    L.lim_smem_bandwidth.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    L.lim_trace_workspace_size.argtypes = [vp, vp, ctypes.POINTER(Params), i32,
+                                           ctypes.POINTER(ctypes.c_size_t)]
+    L.lim_trace.argtypes = [vp, vp, ctypes.POINTER(Params), dbl, u64, u32, u32, i32, vp, i32, vp,
+                            ctypes.c_size_t, vp, vp, vp, vp, vp]
     L.lim_bp_sweeps.argtypes = [vp, ctypes.POINTER(Params), u32, vp, vp, vp, vp, vp, i32, vp,
                                 ctypes.c_size_t, vp]
     L.lim_readout.argtypes = [vp, ctypes.POINTER(Params), u32, vp, vp, vp]
@@ -149,6 +153,23 @@ def params(rule="minsum", feedback="check_move", precision="f32", quant_scale=2.
                   float(clamp), float(tau), float(dt_tick), int(sweeps_per_tick), float(ring_prob),
                   int(tick_budget), int(gauge_on_move), VARIANT[variant], int(block_threads),
                   int(blocks_per_sm), int(profile), int(smem_cap))
+
+
+def default_quant_scale(precision: str, q: float) -> float:
+    """Default integer step Delta (LLR units per step) of the quantised modes.
+
+    int8: one step per prior unit, Delta = |log(q/(1-q))|.  With alpha = 1 every
+    min-sum message is an integer multiple of the prior until it meets the clamp
+    (a message is the prior plus a sum of others, or the signed smallest of
+    others), so this step stores the messages exactly up to the int8 saturation
+    at 127 |pi| (374 LLR at q = 0.05), and the Evidence threshold -log(d-1)
+    rounded up to a step is equivalent on that lattice.  (A step of 2^-2 would
+    saturate at 31.75 LLR.)  int16: 2^-6 (saturation at 512 LLR).  Floating
+    modes ignore it."""
+    import math
+    if precision == "i8":
+        return abs(math.log(q / (1.0 - q)))
+    return 2.0 ** -6
 
 
 def prec_name(prm: Params) -> str:
@@ -283,6 +304,26 @@ def final_words(points) -> int:
     w = ctypes.c_int32()
     check(lib().lim_final_words(pts, len(points), ctypes.byref(w)), "lim_final_words")
     return int(w.value)
+
+
+def plan_describe(ctx: Context, points, prm: Params):
+    """(shape dict, msg_smem per point) of the plan lim_run_batch uses."""
+    pts = _points(points)
+    shape = np.zeros(4, np.int32)
+    smem = np.zeros(max(len(points), 1), np.int32)
+    check(lib().lim_plan_describe(ctx.handle, pts, len(points), ctypes.byref(prm), shape.ctypes.data,
+                                  smem.ctypes.data), "lim_plan_describe")
+    inv = {v: k for k, v in VARIANT.items()}
+    return ({"variant": inv[int(shape[0])], "grid": int(shape[1]), "block": int(shape[2]),
+             "smem_per_block": int(shape[3])}, smem[:len(points)].astype(bool))
+
+
+def smem_bandwidth(ctx: Context):
+    """(copy GB/s, load-only GB/s) of shared memory over every SM (lim_smem_bandwidth)."""
+    c = ctypes.c_double()
+    l_ = ctypes.c_double()
+    check(lib().lim_smem_bandwidth(ctx.handle, ctypes.byref(c), ctypes.byref(l_)), "lim_smem_bandwidth")
+    return c.value, l_.value
 
 
 def workspace_size_host(ctx: Context, points, prm: Params) -> int:
@@ -480,22 +521,40 @@ def sample_noise(code: Code, p: float, seed: int, point_id: int, shot0: int, nsh
 
 
 def trace(ctx: Context, code: Code, prm: Params, p: float, seed: int, point_id: int, shot: int,
-          max_ticks: int):
-    """(e_hist [T+1, nw], s_hist [T+1, mw], record) of one shot, on the host."""
+          max_ticks: int, forced_moves=None, want_l: bool = False):
+    """(e_hist [T+1, nw], s_hist [T+1, mw], record) of one shot, on the host; with
+    ``want_l`` also the per-tick read-out L [T+1, n] (float32, row 0 unused).
+    ``forced_moves`` ((tick, check, qubit) rows, ticks ascending) replaces the
+    machine's own moves (lim_trace replay)."""
     import torch
     dev = torch.device("cuda", ctx.device)
-    ws_bytes = workspace_size(ctx, [(code, p, 1, shot, point_id)], prm)
-    ws = torch.empty(max(ws_bytes, 4096), dtype=torch.uint8, device=dev)
+    fm = None
+    nf = 0
+    if forced_moves is not None:
+        fm = np.ascontiguousarray(np.asarray(forced_moves, dtype=np.int32).reshape(-1, 3))
+        nf = fm.shape[0]
+        if nf == 0:
+            fm = np.zeros((1, 3), np.int32)
+    ws_bytes = ctypes.c_size_t()
+    check(lib().lim_trace_workspace_size(ctx.handle, code.handle, ctypes.byref(prm), nf,
+                                         ctypes.byref(ws_bytes)), "lim_trace_workspace_size")
+    ws = torch.empty(max(int(ws_bytes.value), 4096), dtype=torch.uint8, device=dev)
     eh = torch.zeros((max_ticks + 1) * code.nw, dtype=torch.int32, device=dev)
     sh = torch.zeros((max_ticks + 1) * code.mw, dtype=torch.int32, device=dev)
+    lh = torch.zeros((max_ticks + 1) * code.n, dtype=torch.float32, device=dev) if want_l else None
     rec = torch.zeros(RECORD_DTYPE.itemsize, dtype=torch.uint8, device=dev)
     check(lib().lim_trace(ctx.handle, code.handle, ctypes.byref(prm), float(p), int(seed), int(point_id),
-                          int(shot), int(max_ticks), ws.data_ptr(), ws.numel(), eh.data_ptr(), sh.data_ptr(),
-                          rec.data_ptr(), _stream_ptr(None)), "lim_trace")
+                          int(shot), int(max_ticks), None if fm is None else fm.ctypes.data, nf,
+                          ws.data_ptr(), ws.numel(), eh.data_ptr(), sh.data_ptr(),
+                          None if lh is None else lh.data_ptr(), rec.data_ptr(), _stream_ptr(None)),
+          "lim_trace")
     torch.cuda.synchronize(ctx.device)
     r = np.frombuffer(rec.cpu().numpy().tobytes(), dtype=RECORD_DTYPE)[0]
-    return (eh.cpu().numpy().view(np.uint32).reshape(max_ticks + 1, code.nw),
-            sh.cpu().numpy().view(np.uint32).reshape(max_ticks + 1, code.mw), r)
+    out = (eh.cpu().numpy().view(np.uint32).reshape(max_ticks + 1, code.nw),
+           sh.cpu().numpy().view(np.uint32).reshape(max_ticks + 1, code.mw), r)
+    if want_l:
+        out = out + (lh.cpu().numpy().reshape(max_ticks + 1, code.n),)
+    return out
 
 
 _TORCH_DT = {"f32": "float32", "f16": "float16", "bf16": "bfloat16", "i16": "int16", "i8": "int8"}

@@ -32,7 +32,7 @@ from . import lim
 
 def workload_params(w: dict, precision: str = "f32", rule: str = "", feedback: str = "") -> lim.Params:
     rule = rule or w.get("rule", "minsum")
-    qs = 0.25 if precision == "i8" else 2.0 ** -6
+    qs = lim.default_quant_scale(precision, w["q"])
     return lim.params(rule=rule, feedback=feedback or w.get("feedback", "check_move"),
                       precision=precision,
                       quant_scale=qs, q=w["q"], clamp=w["clamp"], tau=w["tau"],

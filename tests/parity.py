@@ -53,6 +53,25 @@ def final_state(code, prm, p, seed, point_id, shot, tick_budget=0):
     return r["trace"]["e_hist"][T], r
 
 
+def oracle_shots_with_finals(code, op, p, seed, point_id, shot0, nshots):
+    """Records (RECORD_DTYPE) and final errors (bytes [nshots, n]) of the oracle
+    for shots shot0 .. shot0+nshots-1, over a thread pool."""
+    from concurrent.futures import ThreadPoolExecutor
+    oc = O.OracleCode.from_code(code)
+    recs = np.zeros(nshots, dtype=O.RECORD_DTYPE)
+    fins = np.zeros((nshots, code.n), dtype=np.uint8)
+
+    def one(i):
+        r = O.run_shot(oc, op, p, seed, point_id, shot0 + i, trace_ticks=0)
+        for f in O.RECORD_DTYPE.names:
+            recs[i][f] = r[f]
+        fins[i] = r["trace"]["e_final"]
+
+    with ThreadPoolExecutor(max_workers=THREADS) as ex:
+        list(ex.map(one, range(nshots)))
+    return recs, fins
+
+
 def compare_records(gpu, ora, what=""):
     for f in ("t_clr", "converged", "failed", "moves", "ticks", "sweeps"):
         bad = np.nonzero(gpu[f] != ora[f])[0]

@@ -129,3 +129,28 @@ def test_host_context_refuses_compute(L, host):
     c = host.toric2d(4)
     with pytest.raises(L.LimError, match="LIM_E_INVAL"):
         L.workspace_size(host, [(c, 0.05, 10, 0, 0)], L.params())
+
+
+def test_trace_replay_validation(L, host):
+    """lim_trace checks a forced-move list before anything reaches a GPU: ticks
+    must be >= 1 and ascending, qubits inside the code, and only the
+    check-centric rules replay moves.  (Dummy device pointers: every call here
+    is refused before any device access.)"""
+    import ctypes
+    c = host.toric2d(4)
+    dummy = 4096
+
+    def call(prm, moves):
+        fm = np.ascontiguousarray(np.asarray(moves, np.int32).reshape(-1, 3))
+        return L.lib().lim_trace(host.handle, c.handle, ctypes.byref(prm), 0.05, 1, 0, 0, 10,
+                                 fm.ctypes.data, fm.shape[0], dummy, 1 << 20, dummy, dummy, None,
+                                 dummy, None)
+
+    prm = L.params()
+    assert call(prm, [[1, 0, 3], [0, 0, 2]]) == 1   # tick 0
+    assert call(prm, [[2, 0, 3], [1, 0, 2]]) == 1   # descending
+    assert call(prm, [[1, 0, c.n]]) == 1            # qubit out of range
+    assert call(L.params(feedback="bit_discrete"), [[1, 0, 3]]) == 6  # LIM_E_UNSUPPORTED
+    # a valid list passes validation and then meets the host-only context
+    assert call(prm, [[1, 0, 3], [1, 1, 4], [5, 0, 0]]) == 1
+    assert "host-only" in L.lib().lim_last_error().decode()

@@ -1,0 +1,109 @@
+"""Full-size parity: sampled shots of every configuration's largest codes, in the
+launch configuration the benchmark uses (library default shape, all of the
+workload's code sizes in one launch, so the shared-memory plan -- which codes
+keep their messages in shared memory and which stream them from global memory
+-- is the benchmark's), against the oracle shot by shot in the same precision.
+Every integer result (t_clr, converged, failed, moves, ticks, sweeps) and the
+final residual of each sampled shot is bit-exact.
+"""
+import numpy as np
+import pytest
+
+from paper_2609_38139_b300 import inputs as I
+
+from parity import compare_records, oracle_params, oracle_shots_with_finals
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_38139_b300 import build, lim
+    build.build()
+    return lim
+
+
+@pytest.fixture(scope="module")
+def ctx(L):
+    return L.Context(0)
+
+
+def _workload_sample(L, ctx, workload, prec, picks, seed=0, shot0=7000):
+    """One launch over every code of ``workload`` (as the benchmark builds them),
+    with ``picks`` = {size: [(p, shots), ...]} shots; every code of the workload
+    is present (sizes without picks get one shot at their first p), so the plan
+    equals the benchmark's.  Returns the shots compared with the oracle."""
+    w = I.WORKLOADS[workload]
+    qs = L.default_quant_scale(prec, w["q"])
+    prm = L.params(rule=w.get("rule", "minsum"), feedback=w.get("feedback", "check_move"),
+                   precision=prec, quant_scale=qs, q=w["q"], clamp=w["clamp"], tau=w["tau"],
+                   dt_tick=w["dt_tick"], sweeps_per_tick=w["K"], tick_budget=1)
+    pts, meta = [], []
+    pid = 0
+    for size in w["sizes"]:
+        code = I.make_code(w["family"], size)
+        lc = ctx.from_inputs(code)
+        T = I.tick_budget(w["budget"], size, w["dt_tick"])
+        for p, n in picks.get(size, [(w["p"][0], 1)]):
+            pts.append((lc, p, n, shot0, pid, T))
+            meta.append((code, p, n, pid, T))
+            pid += 1
+    # most expensive first, as the benchmark orders its queue
+    order = sorted(range(len(pts)), key=lambda i: -meta[i][0].E * meta[i][4])
+    pts = [pts[i] for i in order]
+    meta = [meta[i] for i in order]
+    assert L.workspace_size(ctx, pts, prm) > 0
+    tal, rec, fin = L.run_batch(ctx, pts, prm, seed, e_final=True)
+    assert int(tal["errors"].sum()) == 0
+    row = 0
+    checked = 0
+    for (code, p, n, pid, T) in meta:
+        op = oracle_params(prm)
+        op.tick_budget = T
+        ora, fins = oracle_shots_with_finals(code, op, p, seed, pid, shot0, n)
+        compare_records(rec[row:row + n], ora, f"{code.name} p={p} {prec}")
+        e_gpu = L.bits_to_bytes(fin[row:row + n], code.n)
+        for i in range(n):
+            assert np.array_equal(e_gpu[i], fins[i]), (code.name, p, i)
+        row += n
+        checked += n
+    return checked
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+def test_full_size_point_sector_L24(L, ctx, prec):
+    """3D toric point sector: L = 24 (global-memory arena, 16-bit rows of six)
+    at a low and a high p, and L = 16 (shared memory under two teams per SM)."""
+    n = _workload_sample(L, ctx, "toric3d_point_sweep", prec,
+                         {24: [(0.01, 1), (0.05, 1)], 16: [(0.03, 2)]})
+    assert n >= 4
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16", "i16"])
+def test_full_size_toric2d_L128_reduced(L, ctx, prec):
+    """2D toric sweep with 16-bit storage: L = 128 (global arena) at p = 0.02
+    and 0.12, L = 64."""
+    n = _workload_sample(L, ctx, "toric2d_sweep", prec,
+                         {128: [(0.02, 1), (0.12, 1)], 64: [(0.08, 2)]})
+    assert n >= 4
+
+
+def test_full_size_membrane_L16_i16(L, ctx):
+    """3D membrane sector, int16 (Delta = 2^-6): L = 16 at the grid's lowest and
+    highest p, budget 10^4 ticks."""
+    n = _workload_sample(L, ctx, "toric3d_membrane_sweep", "i16",
+                         {16: [(0.01, 2), (0.06, 2)], 12: [(0.06, 2)]})
+    assert n >= 6
+
+
+def test_full_size_bb_i8(L, ctx):
+    """Bivariate-bicycle codes, int8 (Delta = |pi|, the default), budget 10^4 ticks: the three
+    codes of the mixed configuration at its lowest and highest p."""
+    picks = {(6, 6): [(0.01, 8), (0.08, 8)], (15, 3): [(0.01, 8), (0.08, 8)],
+             (12, 6): [(0.01, 8), (0.08, 8)]}
+    n = _workload_sample(L, ctx, "bb_mixed", "i8", picks)
+    assert n == 48
