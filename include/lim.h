@@ -94,6 +94,15 @@ extern "C" {
 #define LIM_VARIANT_CTA 1   /* persistent kernel, one thread block per shot                */
 #define LIM_VARIANT_WARP 2  /* persistent kernel, one warp per shot (small codes)          */
 #define LIM_VARIANT_PLAIN 3 /* baseline: one launch per tick, one block per shot, host loop */
+/* Persistent kernel with one shot per lane: the 32 lanes of a warp run 32 shots
+ * of the same code in step, with the shots' messages interleaved in shared
+ * memory.  For small codes; needs the single-qubit check-centric rule with
+ * alpha = 1, no gauge switch on moves, no phase counters, and codes of uniform
+ * degrees (the paper's families).  AUTO takes it when those hold, a warp's 32
+ * shots fit in 56 KB of shared memory and the batch has at least four shots per
+ * lane of the GPU (a warp waits for its lanes' longest shot); block_threads
+ * <= 256. */
+#define LIM_VARIANT_LANE 4
 
 #define LIM_SECTOR_POINT 0    /* 3D toric code, X checks on vertices (weight 6) */
 #define LIM_SECTOR_MEMBRANE 1 /* 3D toric code, X checks on faces (weight 4)    */
@@ -135,7 +144,8 @@ typedef struct {
   int32_t variant;         /* LIM_VARIANT_*                                         */
   int32_t block_threads;   /* 0 = library default: one-block teams of 512 threads,  */
                            /* two per SM (check-centric rule) or 1024 threads, one  */
-                           /* per SM (bit-centric rule); warp teams 256 per block    */
+                           /* per SM (bit-centric rule); warp teams 256 per block;   */
+                           /* one shot per lane 32 per block                         */
   int32_t blocks_per_sm;   /* 0 = as many as fit                                    */
   int32_t profile;         /* 1: accumulate clock cycles per phase into the tally   */
   int32_t smem_cap;        /* CTA variant: max shared memory per block in bytes;    */

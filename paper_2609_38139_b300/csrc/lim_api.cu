@@ -113,7 +113,7 @@ int derive(const lim_params *p, DevParams &o) {
 
 struct Plan {
   int plain = 0;
-  int warp = 0;
+  int warp = 0;  // launch kind: kKindCTA, kKindWarp or kKindLane
   int block = 0;
   int grid = 0;
   size_t smem = 0;
@@ -123,11 +123,33 @@ struct Plan {
   std::vector<const lim_code *> codes;
   std::vector<int> code_of_point;
   std::vector<uint16_t> msg_smem, chk_smem;  // per code
+  LaneSizes lane{};
   size_t workspace = 0;
 };
 
+// The one-shot-per-lane kernel covers the check-centric single-qubit rule with
+// alpha = 1 (fused sweeps), no gauge switch on moves, no phase counters, and
+// codes of uniform degrees with a fused sweep.
+bool lane_eligible(const DevParams &dp, const std::vector<const lim_code *> &codes) {
+  if (dp.feedback != LIM_FB_CHECK_MOVE || dp.multi || dp.gauge_on_move || !dp.alpha_is_one || dp.profile)
+    return false;
+  for (const lim_code *c : codes) {
+    const DevCode &d = c->dev;
+    const bool pair = (d.dc_u == 6 && d.dv_u == 3) || (d.dc_u == 4 && d.dv_u == 2) ||
+                      (d.dc_u == 6 && d.dv_u == 2) || (d.dc_u == 4 && d.dv_u == 4) ||
+                      (d.dc_u == 2 && d.dv_u == 2);
+    if (!pair || !d.partner) return false;
+  }
+  return true;
+}
+
+// A warp of the lane kernel holds 32 shots' messages in shared memory; AUTO takes
+// it when that leaves room for at least four warps per SM.
+constexpr size_t kLaneAutoBytes = 56 * 1024;
+constexpr uint64_t kLaneShotsPerLane = 4;
+
 int make_plan(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,
-              const DevParams &dp, Plan &pl) {
+              const DevParams &dp, Plan &pl, bool allow_lane = true) {
   if (!ctx) return bad(LIM_E_INVAL, "null context");
   if (ctx->device < 0) return bad(LIM_E_INVAL, "host-only context cannot run kernels");
   if (!pts || npts == 0) return bad(LIM_E_INVAL, "no points");
@@ -150,15 +172,34 @@ int make_plan(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_param
   }
   std::vector<CodeLayout> lay;
   size_t max_bits = 0, max_all = 0;
-  int max_E = 0;
+  int max_E = 0, max_nw = 0, max_mw = 0;
   for (auto *c : pl.codes) {
     lay.push_back(code_layout(c->dev, dp.prec));
     const CodeLayout &l = lay.back();
     max_bits = std::max(max_bits, l.bits_bytes);
     max_all = std::max(max_all, l.bits_bytes + l.msg_bytes + l.chk_bytes);
     max_E = std::max(max_E, c->dev.E);
+    max_nw = std::max(max_nw, c->dev.nw);
+    max_mw = std::max(max_mw, c->dev.mw);
   }
   int variant = prm->variant;
+  if (variant == LIM_VARIANT_LANE || variant == LIM_VARIANT_AUTO) {
+    const bool ok = allow_lane && lane_eligible(dp, pl.codes);
+    pl.lane = lane_sizes(max_E, max_nw, max_mw, dp.prec);
+    if (variant == LIM_VARIANT_LANE && !ok)
+      return bad(LIM_E_UNSUPPORTED, "one shot per lane needs the single-qubit check-centric rule with "
+                                    "alpha = 1, no gauge switch on moves, no phase counters, and codes "
+                                    "of uniform degrees");
+    if (variant == LIM_VARIANT_AUTO && ok && pl.lane.total <= kLaneAutoBytes) {
+      // A lane runs its shots one after another, and its warp waits for the
+      // longest: with few shots per lane the longest shots set the launch time.
+      // Take lanes when the batch gives every lane of a full GPU a few shots.
+      uint64_t items = 0;
+      for (uint32_t i = 0; i < npts; i++) items += pts[i].shots;
+      const uint64_t lanes = (uint64_t)ctx->num_sms * ((size_t)ctx->smem_per_sm / pl.lane.total) * 32;
+      if (items >= kLaneShotsPerLane * lanes) variant = LIM_VARIANT_LANE;
+    }
+  }
   if (variant == LIM_VARIANT_PLAIN) {
     // one block per shot, every array in HBM, one point at a time
     if (dp.prec != LIM_PREC_F32) return bad(LIM_E_UNSUPPORTED, "the plain path supports f32 only");
@@ -175,7 +216,20 @@ int make_plan(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_param
     variant = (max_all <= 24 * 1024 && max_E <= 2048) ? LIM_VARIANT_WARP : LIM_VARIANT_CTA;
   pl.msg_smem.assign(pl.codes.size(), 0);
   pl.chk_smem.assign(pl.codes.size(), 0);
-  if (variant == LIM_VARIANT_WARP) {
+  if (variant == LIM_VARIANT_LANE) {
+    pl.warp = kKindLane;
+    // default: one warp per block, so that as many warps fit on an SM as its
+    // shared memory holds (blocks of several warps would round that down)
+    pl.block = prm->block_threads > 0 ? prm->block_threads : 32;
+    if (pl.block % 32 || pl.block > 256) return bad(LIM_E_INVAL, "block_threads must be a multiple of 32, <= 256 for one shot per lane");
+    pl.team_smem = pl.lane.total;
+    pl.smem = pl.team_smem * (size_t)(pl.block / 32);
+    if (pl.smem > (size_t)ctx->smem_optin)
+      return bad(LIM_E_UNSUPPORTED, "codes too large for one shot per lane; use LIM_VARIANT_WARP or _CTA");
+    std::fill(pl.msg_smem.begin(), pl.msg_smem.end(), 1);
+    std::fill(pl.chk_smem.begin(), pl.chk_smem.end(), 1);
+    pl.slot_bytes = 0;
+  } else if (variant == LIM_VARIANT_WARP) {
     pl.warp = 1;
     pl.block = prm->block_threads > 0 ? prm->block_threads : 256;
     if (pl.block % 32 || pl.block > 1024) return bad(LIM_E_INVAL, "block_threads must be a multiple of 32, <= 1024");
@@ -243,7 +297,7 @@ int make_plan(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_param
   if (occ < 1) return bad(LIM_E_UNSUPPORTED, "batch kernel does not fit on an SM with this shape");
   if (prm->blocks_per_sm > 0) occ = std::min(occ, prm->blocks_per_sm);
   pl.grid = ctx->num_sms * occ;
-  pl.n_teams = (size_t)pl.grid * (pl.warp ? pl.block / 32 : 1);
+  pl.n_teams = (size_t)pl.grid * (pl.warp != kKindCTA ? pl.block / 32 : 1);
   pl.workspace = kWsHeader + pl.n_teams * pl.slot_bytes;
   return LIM_OK;
 }
@@ -272,6 +326,24 @@ void fill_args(const Plan &pl, const lim_point *pts, uint32_t npts, const lim_pa
     item += pts[i].shots;
   }
   a.total_items = item;
+  // points grouped by code, with their items numbered within the code
+  int pos = 0;
+  for (size_t c = 0; c < pl.codes.size(); c++) {
+    a.code_pt0[c] = (int16_t)pos;
+    uint64_t acc = 0;
+    for (uint32_t i = 0; i < npts; i++) {
+      if (pl.code_of_point[i] != (int)c) continue;
+      a.cpts[pos++] = (uint8_t)i;
+      a.pts[i].code_item0 = acc;
+      acc += pts[i].shots;
+    }
+    a.code_items[c] = acc;
+  }
+  a.code_pt0[pl.codes.size()] = (int16_t)pos;
+  a.lane_buf = (uint32_t)pl.lane.buf;
+  a.lane_e = (uint32_t)pl.lane.e;
+  a.lane_s = (uint32_t)pl.lane.s;
+  a.lane_s0 = (uint32_t)pl.lane.s0;
   a.team_smem = (uint32_t)pl.team_smem;
   a.slot_bytes = (uint32_t)pl.slot_bytes;
   a.slots = pl.slot_bytes ? (uint8_t *)ws + kWsHeader : nullptr;
@@ -586,7 +658,9 @@ int lim_plan_describe(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const l
     st = make_plan(ctx, pts, npts, prm, dp, pl);
     if (st) return st;
     if (shape) {
-      shape[0] = pl.plain ? LIM_VARIANT_PLAIN : (pl.warp ? LIM_VARIANT_WARP : LIM_VARIANT_CTA);
+      shape[0] = pl.plain ? LIM_VARIANT_PLAIN
+                          : (pl.warp == kKindLane ? LIM_VARIANT_LANE
+                                                  : (pl.warp == kKindWarp ? LIM_VARIANT_WARP : LIM_VARIANT_CTA));
       shape[1] = pl.grid;
       shape[2] = pl.block;
       shape[3] = (int32_t)pl.smem;
@@ -896,7 +970,8 @@ int lim_autotune(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_pa
                             {LIM_VARIANT_CTA, 1024, 1, 48 << 10}, {LIM_VARIANT_CTA, 512, 2, 0},
                             {LIM_VARIANT_CTA, 512, 1, 0},         {LIM_VARIANT_CTA, 256, 4, 0},
                             {LIM_VARIANT_WARP, 256, 0, 0},        {LIM_VARIANT_WARP, 512, 0, 0},
-                            {LIM_VARIANT_WARP, 128, 0, 0}};
+                            {LIM_VARIANT_WARP, 128, 0, 0},        {LIM_VARIANT_LANE, 128, 0, 0},
+                            {LIM_VARIANT_LANE, 64, 0, 0},         {LIM_VARIANT_LANE, 32, 0, 0}};
     double best_rate = -1;
     lim_params best_p = *prm;
     void *ws = nullptr;
@@ -973,12 +1048,15 @@ int lim_trace_workspace_size(lim_ctx *ctx, const lim_code *code, const lim_param
   return guarded([&] {
     if (!code || !prm || !bytes || nforced < 0) return bad(LIM_E_INVAL, "bad argument");
     lim_params one = *prm;
-    if (one.variant == LIM_VARIANT_PLAIN) one.variant = LIM_VARIANT_CTA;
+    if (one.variant == LIM_VARIANT_PLAIN || one.variant == LIM_VARIANT_LANE) one.variant = LIM_VARIANT_CTA;
     lim_point pt = {code, 0.0, 1, 0, 0, 0};
-    size_t ws = 0;
-    int st = lim_workspace_size(ctx, &pt, 1, &one, &ws);
+    DevParams dp;
+    int st = derive(&one, dp);
     if (st) return st;
-    *bytes = a256(ws) + a256((size_t)nforced * 3 * sizeof(int32_t));
+    Plan pl;
+    st = make_plan(ctx, &pt, 1, &one, dp, pl, false);  // traces come from a team kernel
+    if (st) return st;
+    *bytes = a256(pl.workspace) + a256((size_t)nforced * 3 * sizeof(int32_t));
     return LIM_OK;
   });
 }
@@ -1003,9 +1081,10 @@ int lim_trace(lim_ctx *ctx, const lim_code *code, const lim_params *prm, double 
     lim_point pt = {code, p, 1, shot, point_id, 0};
     if (pt.code->dev.m == 0) return bad(LIM_E_INVAL, "empty code");
     lim_params one = *prm;
-    if (one.variant == LIM_VARIANT_PLAIN) one.variant = LIM_VARIANT_CTA;  // traces come from the batch kernel
+    // traces come from a team kernel (one block or one warp per shot)
+    if (one.variant == LIM_VARIANT_PLAIN || one.variant == LIM_VARIANT_LANE) one.variant = LIM_VARIANT_CTA;
     Plan pl;
-    st = make_plan(ctx, &pt, 1, &one, dp, pl);
+    st = make_plan(ctx, &pt, 1, &one, dp, pl, false);
     if (st) return st;
     const size_t forced_off = a256(pl.workspace);
     const size_t need = forced_off + a256((size_t)nforced * 3 * sizeof(int32_t));

@@ -1,11 +1,13 @@
 // lim_batch_f16.cu -- batch kernels with f16 message storage.
 #include "lim_batch.cuh"
+#include "lim_lane.cuh"
 
 namespace lim {
 
-const void *batch_fn_f16(int warp, int rule, int fb) {
+const void *batch_fn_f16(int kind, int rule, int fb) {
   using namespace batch_detail;
-  return warp ? pick_kernel<TeamWarp, LIM_PREC_F16>(rule, fb) : pick_kernel<TeamCTA, LIM_PREC_F16>(rule, fb);
+  if (kind == kKindLane) return fb == LIM_FB_CHECK_MOVE ? lane_detail::pick_lane_kernel<LIM_PREC_F16>(rule) : nullptr;
+  return kind == kKindWarp ? pick_kernel<TeamWarp, LIM_PREC_F16>(rule, fb) : pick_kernel<TeamCTA, LIM_PREC_F16>(rule, fb);
 }
 
 }  // namespace lim

@@ -227,24 +227,28 @@ __device__ __forceinline__ void flip_bits(const DevCode &C, const FlipCtx &F, in
 }
 
 // Min-sum form of Eq. 2 for one check of N inputs: out_j = (-1)^{s_c+d_c} prod_{w!=j}
-// sgn(x_w) min_{w!=j} |x_w|, sgn(0) = +1, a zero magnitude stored as +0.  The two
-// smallest magnitudes are tracked branch-free (ties keep min2 = min1), and the
-// minimum over the others is min2 exactly where |x_j| equals min1.
+// sgn(x_w) min_{w!=j} |x_w|, sgn(0) = +1, a zero magnitude stored as +0.  The
+// minimum over the others is min(prefix minimum before j, suffix minimum after
+// j): exact, with no comparison of equal magnitudes, and shallower dependency
+// chains than tracking the two smallest values.
 template <class A, int N>
 __device__ __forceinline__ void minsum_row(const A (&x)[N], int neg, A (&out)[N]) {
   A a[N];
-  A min1 = inf_of(A(0)), min2 = inf_of(A(0));
 #pragma unroll
   for (int j = 0; j < N; j++) {
     a[j] = absw(x[j]);
     neg ^= (x[j] < A(0));
-    const A t = max(min1, a[j]);
-    min1 = min(min1, a[j]);
-    min2 = min(min2, t);
   }
+  A pre[N], suf[N];
+  pre[0] = a[0];
+#pragma unroll
+  for (int j = 1; j < N - 1; j++) pre[j] = min(pre[j - 1], a[j]);
+  suf[N - 1] = a[N - 1];
+#pragma unroll
+  for (int j = N - 2; j > 0; j--) suf[j] = min(suf[j + 1], a[j]);
 #pragma unroll
   for (int j = 0; j < N; j++) {
-    const A mag = (a[j] == min1) ? min2 : min1;
+    const A mag = (j == 0) ? suf[1] : (j == N - 1) ? pre[N - 2] : min(pre[j - 1], suf[j + 1]);
     const bool ng = neg ^ (x[j] < A(0));
     out[j] = (mag == A(0)) ? A(0) : (ng ? -mag : mag);
   }
@@ -489,6 +493,43 @@ __device__ __forceinline__ typename MT<PREC>::A round_to_storage(typename MT<PRE
   return MT<PREC>::ld(&t);
 }
 
+// Eq. 2 on one check row of the fused sweep: x are the check's qubit->check
+// messages (already clamped and rounded to the storage format), sbit = s~_c;
+// res are the new stored check->qubit messages (alpha = 1: the clamped BP value;
+// a min-sum output is one of the already clamped inputs up to sign, so its clamp
+// is the identity).
+template <int PREC, int RULE, int DC>
+__device__ __forceinline__ void fused_row_out(const DevParams &P, const typename MT<PREC>::A (&x)[DC],
+                                              int sbit, typename MT<PREC>::T (&res)[DC]) {
+  using M = MT<PREC>;
+  using A = typename M::A;
+  A out[DC];
+  constexpr bool kMin = RULE == LIM_RULE_MINSUM || M::is_int;
+  if (kMin) {
+    minsum_row<A, DC>(x, (sbit + DC) & 1, out);
+  } else {
+    if constexpr (!M::is_int) {
+      float pre[DC], suf[DC];
+#pragma unroll
+      for (int j = 0; j < DC; j++) pre[j] = (j == 0) ? x[0] : boxplus(pre[j - 1], x[j]);
+#pragma unroll
+      for (int j = DC - 1; j >= 0; j--) suf[j] = (j == DC - 1) ? x[j] : boxplus(x[j], suf[j + 1]);
+      const float sg = (((sbit + DC) & 1) ? -1.f : 1.f);
+#pragma unroll
+      for (int j = 0; j < DC; j++) {
+        float gg;
+        if (j == 0) gg = suf[1];
+        else if (j == DC - 1) gg = pre[DC - 2];
+        else gg = boxplus(pre[j - 1], suf[j + 1]);
+        gg = sg * gg;
+        out[j] = (gg == 0.f) ? 0.f : gg;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < DC; j++) M::st(res + j, kMin ? out[j] : update(P, A(0), out[j]));
+}
+
 // Gathers of one check: its partner edges and the messages there.
 template <int PREC, int DC, int DV>
 struct FusedIn {
@@ -520,11 +561,11 @@ __device__ __forceinline__ void fused_compute(const DevCode &C, const DevParams 
     // conversions pair up): each qubit->check value is computed in binary32, clamped
     // and rounded once to the storage format as in the float path, and the
     // min-sum row then works on the stored bit patterns -- non-negative values
-    // of one IEEE format order like their patterns, so min1/min2 are exact and
+    // of one IEEE format order like their patterns, so the minima are exact and
     // the outputs need no conversion back.  A -0 input carries no sign (x < 0
     // is false for it in the float path) and a zero output is stored as +0.
     uint32_t a[DC], sgn[DC];
-    uint32_t neg = (sbit + DC) & 1, min1 = 0xffffu, min2 = 0xffffu;
+    uint32_t neg = (sbit + DC) & 1;
 #pragma unroll
     for (int j = 0; j < DC; j++) {
       float acc = pi;
@@ -537,14 +578,19 @@ __device__ __forceinline__ void fused_compute(const DevCode &C, const DevParams 
       a[j] = bits & 0x7fffu;
       sgn[j] = (bits >> 15) & (a[j] != 0u);
       neg ^= sgn[j];
-      const uint32_t t = max(min1, a[j]);
-      min1 = min(min1, a[j]);
-      min2 = min(min2, t);
     }
+    // minimum over the others from prefix and suffix minima (see minsum_row)
+    uint32_t pre[DC], suf[DC];
+    pre[0] = a[0];
+#pragma unroll
+    for (int j = 1; j < DC - 1; j++) pre[j] = min(pre[j - 1], a[j]);
+    suf[DC - 1] = a[DC - 1];
+#pragma unroll
+    for (int j = DC - 2; j > 0; j--) suf[j] = min(suf[j + 1], a[j]);
     uint16_t res[DC];
 #pragma unroll
     for (int j = 0; j < DC; j++) {
-      const uint32_t mag = (a[j] == min1) ? min2 : min1;
+      const uint32_t mag = (j == 0) ? suf[1] : (j == DC - 1) ? pre[DC - 2] : min(pre[j - 1], suf[j + 1]);
       res[j] = (uint16_t)(mag == 0u ? 0u : (mag | ((neg ^ sgn[j]) << 15)));
     }
     RowIO<uint16_t, DC>::store(reinterpret_cast<uint16_t *>(CVn) + (size_t)c * DC, res);
@@ -558,34 +604,8 @@ __device__ __forceinline__ void fused_compute(const DevCode &C, const DevParams 
     for (int jj = 0; jj < DV - 1; jj++) acc = wadd(acc, g.in[j * (DV - 1) + jj]);
     x[j] = round_to_storage<PREC>(update(P, A(0), acc));
   }
-  A out[DC];
-  constexpr bool kMin = RULE == LIM_RULE_MINSUM || M::is_int;
-  if (kMin) {
-    minsum_row<A, DC>(x, (sbit + DC) & 1, out);
-  } else {
-    if constexpr (!M::is_int) {
-      float pre[DC], suf[DC];
-#pragma unroll
-      for (int j = 0; j < DC; j++) pre[j] = (j == 0) ? x[0] : boxplus(pre[j - 1], x[j]);
-#pragma unroll
-      for (int j = DC - 1; j >= 0; j--) suf[j] = (j == DC - 1) ? x[j] : boxplus(x[j], suf[j + 1]);
-      const float sg = (((sbit + DC) & 1) ? -1.f : 1.f);
-#pragma unroll
-      for (int j = 0; j < DC; j++) {
-        float gg;
-        if (j == 0) gg = suf[1];
-        else if (j == DC - 1) gg = pre[DC - 2];
-        else gg = boxplus(pre[j - 1], suf[j + 1]);
-        gg = sg * gg;
-        out[j] = (gg == 0.f) ? 0.f : gg;
-      }
-    }
-  }
   T res[DC];
-  // alpha = 1 here: the new message is the clamped BP value; a min-sum output is
-  // one of the (already clamped) inputs up to sign, so its clamp is the identity
-#pragma unroll
-  for (int j = 0; j < DC; j++) M::st(res + j, kMin ? out[j] : update(P, A(0), out[j]));
+  fused_row_out<PREC, RULE, DC>(P, x, sbit, res);
   RowIO<T, DC>::store(CVn + (size_t)c * DC, res);
 }
 

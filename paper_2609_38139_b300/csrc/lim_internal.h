@@ -50,6 +50,7 @@ struct DevPoint {
   uint16_t chk_smem;   // 1: its per-check feedback scratch lives in shared memory
   uint64_t p_thr;      // floor(p * 2^32), 2^32 for p >= 1
   uint64_t item0;      // first work item of this point
+  uint64_t code_item0; // first item of this point among the items of its code (lane variant)
 };
 
 // Scalars of the method in the working arithmetic (binary32 or int32 steps).
@@ -86,6 +87,14 @@ struct LaunchArgs {
   int32_t trace_ticks;
   const int32_t *forced;   // nullable: replayed moves (tick, check, qubit), ticks ascending
   int32_t nforced;
+  // one shot per lane: a warp's shared memory holds three message buffers of
+  // lane_buf bytes, then the bit vectors e, s, s0 (32 interleaved lanes each);
+  // code c's points are cpts[code_pt0[c] .. code_pt0[c+1]), its items are
+  // numbered 0 .. code_items[c)-1 in that order and handed out from queue[1 + c]
+  uint32_t lane_buf, lane_e, lane_s, lane_s0;
+  uint64_t code_items[LIM_MAX_CODES];
+  int16_t code_pt0[LIM_MAX_CODES + 1];
+  uint8_t cpts[LIM_MAX_POINTS];
   DevCode codes[LIM_MAX_CODES];
   DevPoint pts[LIM_MAX_POINTS];
 };
@@ -124,12 +133,17 @@ int build_bb(int32_t l, int32_t m, const int32_t *a_xy, const int32_t *b_xy, Hos
 
 void set_error(const std::string &msg);
 
-// Kernel launchers (lim_kernels.cu).
-int launch_batch(const LaunchArgs &args, int variant_warp, int grid, int block, size_t smem,
-                 void *stream);
-const void *batch_fn_ptr(int warp, int prec, int rule, int fb);
-int batch_occupancy(int warp, int prec, int rule, int fb, int block, size_t smem,
-                    int *blocks_per_sm);
+// Kernel launchers (lim_kernels.cu).  kind: 0 one block per shot, 1 one warp
+// per shot, 2 one lane per shot.
+constexpr int kKindCTA = 0, kKindWarp = 1, kKindLane = 2;
+int launch_batch(const LaunchArgs &args, int kind, int grid, int block, size_t smem, void *stream);
+const void *batch_fn_ptr(int kind, int prec, int rule, int fb);
+int batch_occupancy(int kind, int prec, int rule, int fb, int block, size_t smem, int *blocks_per_sm);
+// Shared memory of one warp of the lane kernel for codes of at most these sizes.
+struct LaneSizes {
+  size_t buf, e, s, s0, total;
+};
+LaneSizes lane_sizes(int E_max, int nw_max, int mw_max, int prec);
 // Plain baseline: per-shot HBM slot size, and the init / tick / finish kernels.
 size_t plain_slot_bytes(const DevCode &c, int prec);
 int launch_plain(const LaunchArgs &args, int kind, int t, int *running, int grid, int block,

@@ -11,22 +11,22 @@
 
 namespace lim {
 
-const void *batch_fn_f32(int warp, int rule, int fb);
-const void *batch_fn_f16(int warp, int rule, int fb);
-const void *batch_fn_bf16(int warp, int rule, int fb);
-const void *batch_fn_i16(int warp, int rule, int fb);
-const void *batch_fn_i8(int warp, int rule, int fb);
+const void *batch_fn_f32(int kind, int rule, int fb);
+const void *batch_fn_f16(int kind, int rule, int fb);
+const void *batch_fn_bf16(int kind, int rule, int fb);
+const void *batch_fn_i16(int kind, int rule, int fb);
+const void *batch_fn_i8(int kind, int rule, int fb);
 void plain_fns_f32(int rule, int fb, const void **init, const void **tick, const void **finish);
 
 namespace {
 
-const void *batch_fn(int warp, int prec, int rule, int fb) {
+const void *batch_fn(int kind, int prec, int rule, int fb) {
   switch (prec) {
-    case LIM_PREC_F32: return batch_fn_f32(warp, rule, fb);
-    case LIM_PREC_F16: return batch_fn_f16(warp, rule, fb);
-    case LIM_PREC_BF16: return batch_fn_bf16(warp, rule, fb);
-    case LIM_PREC_I16: return batch_fn_i16(warp, rule, fb);
-    case LIM_PREC_I8: return batch_fn_i8(warp, rule, fb);
+    case LIM_PREC_F32: return batch_fn_f32(kind, rule, fb);
+    case LIM_PREC_F16: return batch_fn_f16(kind, rule, fb);
+    case LIM_PREC_BF16: return batch_fn_bf16(kind, rule, fb);
+    case LIM_PREC_I16: return batch_fn_i16(kind, rule, fb);
+    case LIM_PREC_I8: return batch_fn_i8(kind, rule, fb);
   }
   return nullptr;
 }
@@ -123,11 +123,25 @@ CodeLayout code_layout(const DevCode &c, int prec) {
   return L;
 }
 
-const void *batch_fn_ptr(int warp, int prec, int rule, int fb) { return batch_fn(warp, prec, rule, fb); }
+const void *batch_fn_ptr(int kind, int prec, int rule, int fb) { return batch_fn(kind, prec, rule, fb); }
 
-int batch_occupancy(int warp, int prec, int rule, int fb, int block, size_t smem,
+LaneSizes lane_sizes(int E_max, int nw_max, int mw_max, int prec) {
+  LaneSizes z;
+  z.buf = a16((size_t)E_max * 32 * msg_bytes_dev(prec));
+  z.e = 3 * z.buf;
+  z.s = z.e + (size_t)nw_max * 32 * 4;
+  z.s0 = z.s + (size_t)mw_max * 32 * 4;
+  z.total = a16(z.s0 + (size_t)mw_max * 32 * 4);
+  return z;
+}
+
+int batch_occupancy(int kind, int prec, int rule, int fb, int block, size_t smem,
                     int *blocks_per_sm) {
-  const void *fn = batch_fn(warp, prec, rule, fb);
+  const void *fn = batch_fn(kind, prec, rule, fb);
+  if (!fn) {
+    set_error("no kernel for this precision/rule/feedback and launch kind");
+    return LIM_E_UNSUPPORTED;
+  }
   cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return cuda_fail(err, "cudaFuncSetAttribute");
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
@@ -135,8 +149,8 @@ int batch_occupancy(int warp, int prec, int rule, int fb, int block, size_t smem
   return LIM_OK;
 }
 
-int launch_batch(const LaunchArgs &args, int warp, int grid, int block, size_t smem, void *stream) {
-  const void *fn = batch_fn(warp, args.prm.prec, args.prm.rule, kernel_feedback(args.prm));
+int launch_batch(const LaunchArgs &args, int kind, int grid, int block, size_t smem, void *stream) {
+  const void *fn = batch_fn(kind, args.prm.prec, args.prm.rule, kernel_feedback(args.prm));
   if (!fn) {
     set_error("no kernel for this precision/rule/feedback");
     return LIM_E_UNSUPPORTED;

@@ -421,7 +421,7 @@ WORKLOADS = {
     # bivariate-bicycle codes, int8 quantised min-sum, 1e6 shots mixed over 27 points.
     "bb_mixed": dict(family="bb", sizes=[(6, 6), (15, 3), (12, 6)], p=p_grid(0.01, 0.08, 9),
                      shots=1000000 // 27, q=0.05, clamp=1000.0, tau=0.1, dt_tick=0.1, K=1,
-                     budget=10000, bench_shots=1024),
+                     budget=10000, bench_shots=1000000 // 27),
     # Table S1 discretisations (fine dt, relaxation alpha = dt/tau, budget t_max/dt) with the
     # paper's check rule (sum-product, Eq. 2) at the smaller sizes of each family; t_max = 1000
     # also for the families the table leaves open.

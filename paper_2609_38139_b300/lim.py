@@ -22,7 +22,7 @@ STATUS = {0: "LIM_OK", 1: "LIM_E_INVAL", 2: "LIM_E_NOMEM", 3: "LIM_E_CUDA", 4: "
 RULE = {"minsum": 0, "sumproduct": 1}
 FEEDBACK = {"check_move": 0, "bit_discrete": 1, "check_move_multi": 2}
 PREC = {"f32": 1, "f16": 2, "bf16": 3, "i16": 4, "i8": 5}
-VARIANT = {"auto": 0, "cta": 1, "warp": 2, "plain": 3}
+VARIANT = {"auto": 0, "cta": 1, "warp": 2, "plain": 3, "lane": 4}
 SECTOR = {"point": 0, "membrane": 1}
 MSG_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "i16": 2, "i8": 1}
 HIST_BINS = 24
