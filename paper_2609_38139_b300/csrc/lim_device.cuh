@@ -530,6 +530,99 @@ __device__ __forceinline__ void fused_row_out(const DevParams &P, const typename
   for (int j = 0; j < DC; j++) M::st(res + j, kMin ? out[j] : update(P, A(0), out[j]));
 }
 
+// Min-sum form of Eq. 2 on one check row of the fused sweep (alpha = 1), from
+// the raw qubit->check sums y_j = pi + sum of the partner messages (Eq. 1) in
+// the working arithmetic.  The stored value of the qubit->check message would be
+// x_j = round(clamp(y_j)) (clamp at CLAMP, Sec. S4; rounding to the storage
+// format, monotone), so |x_j| = min(|round(y_j)|, round(CLAMP)) and x_j has the
+// sign of y_j: the clamp is applied once to each output magnitude, the sign
+// parity is an exclusive-or of sign bits, and the signed output is assembled
+// from bits.  A zero input forces every other output to magnitude zero, so
+// whether it carries a sign bit (-0) never shows.  Results are those of
+// clamping, rounding and minsum_row.
+template <int PREC, int DC>
+__device__ __forceinline__ void fused_minsum_row(const DevParams &P, const typename MT<PREC>::A (&y)[DC],
+                                                 int sbit, typename MT<PREC>::T (&res)[DC]) {
+  using M = MT<PREC>;
+  using T = typename M::T;
+  if constexpr (PREC == LIM_PREC_F32) {
+    uint32_t neg = (uint32_t)((sbit + DC) & 1) << 31;
+    float a[DC];
+#pragma unroll
+    for (int j = 0; j < DC; j++) {
+      neg ^= __float_as_uint(y[j]);
+      a[j] = fabsf(y[j]);
+    }
+    float pre[DC], suf[DC];
+    pre[0] = a[0];
+#pragma unroll
+    for (int j = 1; j < DC - 1; j++) pre[j] = fminf(pre[j - 1], a[j]);
+    suf[DC - 1] = a[DC - 1];
+#pragma unroll
+    for (int j = DC - 2; j > 0; j--) suf[j] = fminf(suf[j + 1], a[j]);
+#pragma unroll
+    for (int j = 0; j < DC; j++) {
+      float mag = (j == 0) ? suf[1] : (j == DC - 1) ? pre[DC - 2] : fminf(pre[j - 1], suf[j + 1]);
+      mag = fminf(mag, P.clamp_f);
+      const uint32_t mb = __float_as_uint(mag);
+      const uint32_t sg = (neg ^ __float_as_uint(y[j])) & 0x80000000u;
+      const uint32_t nz = mb + 0x7fffffffu;  // bit 31 set iff mag > 0
+      res[j] = __uint_as_float(mb | (sg & nz));
+    }
+  } else if constexpr (PREC == LIM_PREC_F16 || PREC == LIM_PREC_BF16) {
+    uint32_t h[DC], a[DC];
+    uint32_t neg = (uint32_t)((sbit + DC) & 1) << 15;
+#pragma unroll
+    for (int j = 0; j < DC; j++) {
+      if constexpr (PREC == LIM_PREC_F16) h[j] = __half_as_ushort(__float2half_rn(y[j]));
+      else h[j] = __bfloat16_as_ushort(__float2bfloat16_rn(y[j]));
+      neg ^= h[j];
+      a[j] = h[j] & 0x7fffu;  // non-negative values of one format order like their patterns
+    }
+    uint32_t cpat;
+    if constexpr (PREC == LIM_PREC_F16) cpat = __half_as_ushort(__float2half_rn(P.clamp_f));
+    else cpat = __bfloat16_as_ushort(__float2bfloat16_rn(P.clamp_f));
+    uint32_t pre[DC], suf[DC];
+    pre[0] = a[0];
+#pragma unroll
+    for (int j = 1; j < DC - 1; j++) pre[j] = min(pre[j - 1], a[j]);
+    suf[DC - 1] = a[DC - 1];
+#pragma unroll
+    for (int j = DC - 2; j > 0; j--) suf[j] = min(suf[j + 1], a[j]);
+    uint16_t r[DC];
+#pragma unroll
+    for (int j = 0; j < DC; j++) {
+      uint32_t mag = (j == 0) ? suf[1] : (j == DC - 1) ? pre[DC - 2] : min(pre[j - 1], suf[j + 1]);
+      mag = min(mag, cpat);
+      const uint32_t sg = (neg ^ h[j]) & 0x8000u;
+      const uint32_t nz = mag + 0x7fffu;  // bit 15 set iff mag > 0
+      r[j] = (uint16_t)(mag | (sg & nz));
+    }
+    memcpy(res, r, sizeof(r));
+  } else {
+    int32_t neg = ((sbit + DC) & 1) ? -1 : 0;  // sign parity in the sign bit
+    int32_t a[DC];
+#pragma unroll
+    for (int j = 0; j < DC; j++) {
+      neg ^= y[j];
+      a[j] = abs(y[j]);
+    }
+    int32_t pre[DC], suf[DC];
+    pre[0] = a[0];
+#pragma unroll
+    for (int j = 1; j < DC - 1; j++) pre[j] = min(pre[j - 1], a[j]);
+    suf[DC - 1] = a[DC - 1];
+#pragma unroll
+    for (int j = DC - 2; j > 0; j--) suf[j] = min(suf[j + 1], a[j]);
+#pragma unroll
+    for (int j = 0; j < DC; j++) {
+      int32_t mag = (j == 0) ? suf[1] : (j == DC - 1) ? pre[DC - 2] : min(pre[j - 1], suf[j + 1]);
+      mag = min(mag, P.clamp_q);
+      res[j] = (T)(((neg ^ y[j]) < 0) ? -mag : mag);
+    }
+  }
+}
+
 // Gathers of one check: its partner edges and the messages there.
 template <int PREC, int DC, int DV>
 struct FusedIn {
@@ -555,57 +648,23 @@ __device__ __forceinline__ void fused_compute(const DevCode &C, const DevParams 
   using T = typename M::T;
   using A = typename M::A;
   const A pi = prior<A>(P);
-  if constexpr ((PREC == LIM_PREC_F16 || PREC == LIM_PREC_BF16) && RULE == LIM_RULE_MINSUM && DC >= 6) {
-    // 16-bit storage, rows of six or more (3D point sector, BB: 12-14 % faster;
-    // for rows of four the float row below measured faster, its output
-    // conversions pair up): each qubit->check value is computed in binary32, clamped
-    // and rounded once to the storage format as in the float path, and the
-    // min-sum row then works on the stored bit patterns -- non-negative values
-    // of one IEEE format order like their patterns, so the minima are exact and
-    // the outputs need no conversion back.  A -0 input carries no sign (x < 0
-    // is false for it in the float path) and a zero output is stored as +0.
-    uint32_t a[DC], sgn[DC];
-    uint32_t neg = (sbit + DC) & 1;
-#pragma unroll
-    for (int j = 0; j < DC; j++) {
-      float acc = pi;
-#pragma unroll
-      for (int jj = 0; jj < DV - 1; jj++) acc = wadd(acc, g.in[j * (DV - 1) + jj]);
-      acc = fminf(fmaxf(acc, -P.clamp_f), P.clamp_f);  // alpha = 1: the update is the clamp
-      uint32_t bits;
-      if constexpr (PREC == LIM_PREC_F16) bits = __half_as_ushort(__float2half_rn(acc));
-      else bits = __bfloat16_as_ushort(__float2bfloat16_rn(acc));
-      a[j] = bits & 0x7fffu;
-      sgn[j] = (bits >> 15) & (a[j] != 0u);
-      neg ^= sgn[j];
-    }
-    // minimum over the others from prefix and suffix minima (see minsum_row)
-    uint32_t pre[DC], suf[DC];
-    pre[0] = a[0];
-#pragma unroll
-    for (int j = 1; j < DC - 1; j++) pre[j] = min(pre[j - 1], a[j]);
-    suf[DC - 1] = a[DC - 1];
-#pragma unroll
-    for (int j = DC - 2; j > 0; j--) suf[j] = min(suf[j + 1], a[j]);
-    uint16_t res[DC];
-#pragma unroll
-    for (int j = 0; j < DC; j++) {
-      const uint32_t mag = (j == 0) ? suf[1] : (j == DC - 1) ? pre[DC - 2] : min(pre[j - 1], suf[j + 1]);
-      res[j] = (uint16_t)(mag == 0u ? 0u : (mag | ((neg ^ sgn[j]) << 15)));
-    }
-    RowIO<uint16_t, DC>::store(reinterpret_cast<uint16_t *>(CVn) + (size_t)c * DC, res);
-    return;
-  }
-  A x[DC];
+  A y[DC];
 #pragma unroll
   for (int j = 0; j < DC; j++) {
     A acc = pi;
 #pragma unroll
     for (int jj = 0; jj < DV - 1; jj++) acc = wadd(acc, g.in[j * (DV - 1) + jj]);
-    x[j] = round_to_storage<PREC>(update(P, A(0), acc));
+    y[j] = acc;
   }
   T res[DC];
-  fused_row_out<PREC, RULE, DC>(P, x, sbit, res);
+  if constexpr (RULE == LIM_RULE_MINSUM || M::is_int) {
+    fused_minsum_row<PREC, DC>(P, y, sbit, res);
+  } else {
+    A x[DC];
+#pragma unroll
+    for (int j = 0; j < DC; j++) x[j] = round_to_storage<PREC>(update(P, A(0), y[j]));
+    fused_row_out<PREC, RULE, DC>(P, x, sbit, res);
+  }
   RowIO<T, DC>::store(CVn + (size_t)c * DC, res);
 }
 

@@ -241,16 +241,24 @@ __device__ __forceinline__ void lane_sweep_group(const DevCode &C, const DevPara
     }
 #pragma unroll
   for (int b = 0; b < NB; b++) {
-    A x[DC];
+    A y[DC];
 #pragma unroll
     for (int j = 0; j < DC; j++) {
       A acc = pi;
 #pragma unroll
       for (int jj = 0; jj < DV - 1; jj++) acc = wadd(acc, in[b][j * (DV - 1) + jj]);
-      x[j] = round_to_storage<PREC>(update(P, A(0), acc));
+      y[j] = acc;
     }
     T res[DC];
-    fused_row_out<PREC, RULE, DC>(P, x, (sw >> ((c0 + b) & 31)) & 1, res);
+    const int sbit = (sw >> ((c0 + b) & 31)) & 1;
+    if constexpr (RULE == LIM_RULE_MINSUM || M::is_int) {
+      fused_minsum_row<PREC, DC>(P, y, sbit, res);
+    } else {
+      A x[DC];
+#pragma unroll
+      for (int j = 0; j < DC; j++) x[j] = round_to_storage<PREC>(update(P, A(0), y[j]));
+      fused_row_out<PREC, RULE, DC>(P, x, sbit, res);
+    }
 #pragma unroll
     for (int j = 0; j < DC; j++) {
       T r = res[j];

@@ -13,15 +13,17 @@ namespace {
 constexpr int kProbeThreads = 1024;
 constexpr int kProbeUnroll = 8;
 
+// .volatile: every access is performed (the assembler may neither hoist a
+// repeated load out of the loop nor forward a stored value to a later load)
 __device__ __forceinline__ void lds128(uint32_t addr, uint4 &v) {
-  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+  asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
                : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                : "r"(addr)
                : "memory");
 }
 __device__ __forceinline__ void sts128(uint32_t addr, const uint4 &v) {
-  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
-               "r"(v.w)
+  asm volatile("st.volatile.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w)
                : "memory");
 }
 
