@@ -45,6 +45,8 @@ from paper_2609_38139_b300 import inputs as I  # noqa: E402
 METRIC = "shot-ticks/s & msg-updates/s vs HBM/SMEM roofline; batched+lowprec vs plain at equal P_L"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
+# the launch shape is tuned on a whole step when a step has at most this many shots
+TUNE_MAX_SHOTS = 40000
 
 
 def workload(name: str, shots: int, sizes=None, ps=None):
@@ -283,7 +285,9 @@ def main():
                     help="K (default: the workload's); relaxation alpha = dt / (K tau)")
     ap.add_argument("--smem-cap", type=int, default=0, help="max shared memory per block in bytes (0 automatic, <0 all that fits)")
     ap.add_argument("--phases", action="store_true", help="report the kernel's per-phase cycle shares")
-    ap.add_argument("--autotune", action="store_true", help="pick the launch shape with lim_autotune")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the library's default launch shape instead of the one lim_autotune picks")
+
     ap.add_argument("--print-source-hash", action="store_true")
     ap.add_argument("--sizes", default="", help="comma list restricting the code sizes")
     ap.add_argument("--ps", default="", help="comma list restricting the error rates")
@@ -331,6 +335,22 @@ def main():
         prm.smem_cap = args.smem_cap
         return prm
 
+    def tuned_params(prec, variant=None):
+        """The arm's parameters with the launch shape lim_autotune picks on a sample
+        of this step's points (untimed); the shape never changes results."""
+        prm = make_params(prec, variant)
+        if args.block_threads or args.blocks_per_sm or args.smem_cap:
+            return prm, "given"
+        if args.no_autotune or args.shots * len(pts) > TUNE_MAX_SHOTS:
+            return prm, "library default"
+        # tuned on the step itself: every shape times the shots of step 0 to the end
+        best, rate = L.autotune(ctx, step_points(0), prm, sample_shots=args.shots, sample_ticks=0)
+        best.profile = prm.profile
+        return best, {"tuned_by": "lim_autotune", "variant": {v: k for k, v in L.VARIANT.items()}[int(best.variant)],
+                      "block_threads": int(best.block_threads), "blocks_per_sm": int(best.blocks_per_sm),
+                      "smem_cap": int(best.smem_cap), "tuning_rate_shot_ticks_per_s": rate,
+                      "sample": "the shots of step 0, run to the end, once per shape (untimed)"}
+
     prm = make_params(args.precision)
 
     # weak scaling: every rank runs its own disjoint shot ids of every point;
@@ -341,14 +361,7 @@ def main():
         return [(codes[(d["family"], d["size"])], d["p"], n, base, d["point_id"], d["T"])
                 for d in pts]
 
-    tuned = None
-    if args.autotune:
-        best, rate = L.autotune(ctx, step_points(0), prm, sample_shots=8, sample_ticks=128)
-        best.profile = prm.profile
-        prm = best
-        tuned = {"variant": int(prm.variant), "block_threads": int(prm.block_threads),
-                 "blocks_per_sm": int(prm.blocks_per_sm), "smem_cap": int(prm.smem_cap),
-                 "sample_rate": rate}
+    prm, tuned = tuned_params(args.precision)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 126 MB L2
 
@@ -411,9 +424,8 @@ def main():
 
     hbm, hbm_src = peak_hbm()
     smem_copy_gbs, smem_load_gbs = L.smem_bandwidth(ctx)
-    _, msg_smem = L.plan_describe(ctx, step_points(0), prm)
 
-    def roofline(arm, prec, tot_ms):
+    def roofline(arm, prec, tot_ms, arm_prm):
         """Roofline of the batch kernel per memory class: codes whose messages live
         in shared memory against the measured shared-memory copy bandwidth, codes
         whose messages live in global memory against the measured HBM copy
@@ -421,7 +433,7 @@ def main():
         Algorithmic bytes: 2 x b per message update (read the old message, write the
         new one)."""
         bpm = L.MSG_BYTES[prec]
-        _, sm = L.plan_describe(ctx, step_points(0), make_params(prec))
+        _, sm = L.plan_describe(ctx, step_points(0), arm_prm)
         upd_pt = np.sum([a["msg_updates"] for a in arm["tallies"]], axis=0).astype(np.float64)
         b_smem = float(upd_pt[sm].sum()) * 2 * bpm / world
         b_glob = float(upd_pt[~sm].sum()) * 2 * bpm / world
@@ -456,12 +468,12 @@ def main():
             "dtype": args.precision, "data": "synthetic",
             "config": dict(arm_config(args, w, len(pts)),
                            parallelism=f"replicas x{world}, disjoint shot ids",
-                           launch_shape=tuned or "library default"),
+                           launch_shape=tuned),
             "sample": f"{args.shots} fresh shot ids of every point per step "
                       f"({args.shots * len(pts)} shots per launch, one launch per step)",
             "msg_updates_per_s": upd / (tot_ms / 1000.0),
             "ler_sample": fails / max(1, shots),
-            "roofline": roofline(main_arm, args.precision, tot_ms),
+            "roofline": roofline(main_arm, args.precision, tot_ms, prm),
             "smem_peak": {"copy_gbs": smem_copy_gbs, "load_gbs": smem_load_gbs,
                           "how": "lim_smem_bandwidth: two 1024-thread blocks per SM moving 16-byte "
                                  "words in shared memory, best of three launches"},
@@ -480,14 +492,16 @@ def main():
     arms = {args.precision: main_arm}
     lowprec = {}
     for lp in low:
-        arm = timed_arm(make_params(lp))
+        lp_prm, lp_shape = tuned_params(lp)
+        arm = timed_arm(lp_prm)
         arms[lp] = arm
         a_ms, a_ticks, a_upd, a_shots, a_fails = reduce_arm(arm)
         lowprec[lp] = {"value": a_ticks / (a_ms / 1000.0), "unit": "shot-ticks/s",
                        "ms_per_step": a_ms / args.steps,
                        "msg_updates_per_s": a_upd / (a_ms / 1000.0),
                        "ler_sample": a_fails / max(1, a_shots),
-                       "roofline": roofline(arm, lp, a_ms)}
+                       "launch_shape": lp_shape,
+                       "roofline": roofline(arm, lp, a_ms, lp_prm)}
     if lowprec:
         line["lowprec"] = lowprec
     clk = clocks.stop()

@@ -321,13 +321,15 @@ int lim_graph_create_from(lim_ctx *ctx, const lim_point *pts, uint32_t npts, con
 int lim_graph_launch(lim_graph *graph, uint64_t seed, uint32_t shot_offset, void *stream);
 int lim_graph_destroy(lim_graph *graph);
 
-/* Autotuner: times the persistent kernel's launch shapes (one block or one warp
- * per shot, block sizes, blocks per SM, shared-memory caps) on a sample of the
- * batch -- every point with at most sample_ticks ticks and, per shape,
- * max(sample_shots, two shots per team of that shape / npts) shots (at most the
- * point's own), so each shape is timed with all its teams busy -- and writes
- * the fastest into best->variant / block_threads / blocks_per_sm (the other
- * fields are copied from prm).  Results never depend on the shape (randomness
+/* Autotuner: times the persistent kernel's launch shapes (one block, one warp or
+ * one lane per shot, block sizes, blocks per SM, shared-memory caps) on one
+ * sample of the batch -- every point with at most sample_ticks ticks (<= 0: the
+ * point's budget) and max(sample_shots, two shots per team of the shape with
+ * the most teams / npts) shots (at most the point's own), the same for every
+ * shape so that their rates compare -- and writes the fastest into
+ * best->variant / block_threads / blocks_per_sm / smem_cap (the other fields
+ * are copied from prm).  A sample of the batch itself (sample_shots = the
+ * points' shots, sample_ticks = 0) times exactly the batch.  Results never depend on the shape (randomness
  * is keyed by shot), only speed does.  Allocates and frees its own scratch,
  * synchronises the device; rate_out (nullable) gets the best shot-ticks/s. */
 int lim_autotune(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_params *prm,

@@ -948,10 +948,10 @@ int lim_autotune(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_pa
   return guarded([&] {
     if (!ctx || !pts || !prm || !best || npts == 0) return bad(LIM_E_INVAL, "null argument");
     if (ctx->device < 0) return bad(LIM_E_INVAL, "host-only context cannot run kernels");
-    // The sample of a shape: every point with at most sample_ticks ticks and
-    // max(sample_shots, enough shots for two per team of that shape) shots (at
-    // most the point's own), so that shapes with many small teams are timed
-    // busy, as the full batch would keep them.
+    // The sample: every point with at most sample_ticks ticks and
+    // max(sample_shots, two shots per team of the shape with the most teams)
+    // shots (at most the point's own) -- the same sample for every shape, so
+    // that their rates compare, and one that keeps every shape's teams busy.
     std::vector<lim_point> sample(pts, pts + npts);
     const auto make_sample = [&](size_t n_teams) {
       const uint64_t per_point = std::max<uint64_t>(sample_shots, (2 * n_teams + npts - 1) / npts);
@@ -972,6 +972,19 @@ int lim_autotune(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_pa
                             {LIM_VARIANT_WARP, 256, 0, 0},        {LIM_VARIANT_WARP, 512, 0, 0},
                             {LIM_VARIANT_WARP, 128, 0, 0},        {LIM_VARIANT_LANE, 128, 0, 0},
                             {LIM_VARIANT_LANE, 64, 0, 0},         {LIM_VARIANT_LANE, 32, 0, 0}};
+    size_t most_teams = 1;
+    for (const Shape &sh : shapes) {
+      lim_params p = *prm;
+      p.variant = sh.variant;
+      p.block_threads = sh.block;
+      p.blocks_per_sm = sh.bpsm;
+      p.smem_cap = sh.cap;
+      DevParams dp;
+      Plan pl;
+      if (derive(&p, dp) == LIM_OK && make_plan(ctx, pts, npts, &p, dp, pl) == LIM_OK)
+        most_teams = std::max(most_teams, pl.warp == kKindLane ? (size_t)pl.grid : pl.n_teams);
+    }
+    make_sample(most_teams);
     double best_rate = -1;
     lim_params best_p = *prm;
     void *ws = nullptr;
@@ -992,7 +1005,6 @@ int lim_autotune(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_pa
       DevParams dp;
       Plan pl;
       if (derive(&p, dp) != LIM_OK || make_plan(ctx, pts, npts, &p, dp, pl) != LIM_OK) continue;  // shape does not fit
-      make_sample(pl.n_teams);
       size_t need = 0;
       if (lim_workspace_size(ctx, sample.data(), npts, &p, &need) != LIM_OK) continue;
       if (need > ws_bytes) {
