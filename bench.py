@@ -404,7 +404,7 @@ def main():
             assert int(a["errors"].sum()) == 0, "device-side error counter set"
         recs = np.frombuffer(rec0.cpu().numpy().tobytes()[:batch.nshots * L.RECORD_DTYPE.itemsize],
                              dtype=L.RECORD_DTYPE).copy()
-        return {"ms": sum(ms), "tallies": arrs, "rec0": recs}
+        return {"ms": sum(ms), "tallies": arrs, "rec0": recs, "ms_steps": ms}
 
     def reduce_arm(arm):
         """Whole-job totals of an arm: max of the ranks' device times, sums of work."""
@@ -471,6 +471,7 @@ def main():
                            launch_shape=tuned),
             "sample": f"{args.shots} fresh shot ids of every point per step "
                       f"({args.shots * len(pts)} shots per launch, one launch per step)",
+            "ms_steps": [round(x, 3) for x in main_arm["ms_steps"]],
             "msg_updates_per_s": upd / (tot_ms / 1000.0),
             "ler_sample": fails / max(1, shots),
             "roofline": roofline(main_arm, args.precision, tot_ms, prm),
@@ -512,8 +513,8 @@ def main():
     # on the shots of step 0, and every batched arm's failures on those shots
     if not args.no_plain and world == 1:
         # the plain path runs one point at a time with a host round trip per tick:
-        # at most 32 shots of every point (the first shot ids of step 0)
-        pshots = min(args.shots, 32)
+        # at most 4096 shots of every point (the first shot ids of step 0)
+        pshots = min(args.shots, 4096)
         plain_prm = make_params("f32", variant="plain")
         pb = L.Batch(ctx, step_points(0, pshots), plain_prm, records=True)
         torch.cuda.synchronize()

@@ -417,7 +417,7 @@ WORKLOADS = {
     "toric3d_membrane_sweep": dict(family="toric3d_membrane", sizes=[6, 8, 12, 16],
                                    p=p_grid(0.01, 0.06, 9), shots=100000, q=0.125,
                                    clamp=1000.0, tau=0.1, dt_tick=0.1, K=1, budget=10000,
-                                   bench_shots=512),
+                                   bench_shots=2048),
     # bivariate-bicycle codes, int8 quantised min-sum, 1e6 shots mixed over 27 points.
     "bb_mixed": dict(family="bb", sizes=[(6, 6), (15, 3), (12, 6)], p=p_grid(0.01, 0.08, 9),
                      shots=1000000 // 27, q=0.05, clamp=1000.0, tau=0.1, dt_tick=0.1, K=1,
