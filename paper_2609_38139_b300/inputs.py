@@ -394,7 +394,9 @@ def p_grid(lo: float, hi: float, npts: int) -> List[float]:
 
 
 # ``bench_shots``: shots per point in one benchmark step (default 32), enough to
-# keep every team of the GPU busy through the uneven termination of the shots.
+# keep every team of the GPU busy through the uneven termination of the shots (the
+# 2D sweep: at 32 per point a step ends with a second wave of the longest L = 128
+# shots on a few teams; from 128 per point the rate is that of larger batches).
 WORKLOADS = {
     # 2D toric code L=8, p=0.05, 1000 shots, tick budget 4L; min-sum FP32.
     "toric2d_L8_small": dict(family="toric2d", sizes=[8], p=[0.05], shots=1000, bench_shots=1000,
@@ -407,7 +409,7 @@ WORKLOADS = {
     # batched 2D toric sweep, L in {16,32,64,128}, 11 p points in 0.02-0.12.
     "toric2d_sweep": dict(family="toric2d", sizes=[16, 32, 64, 128], p=p_grid(0.02, 0.12, 11),
                           shots=100000, q=0.05, clamp=1000.0, tau=0.1, dt_tick=0.1, K=1,
-                          budget="40L"),
+                          budget="40L", bench_shots=128),
     # 3D toric point-like sector, 16-bit messages.
     "toric3d_point_sweep": dict(family="toric3d_point", sizes=[8, 12, 16, 24],
                                 p=p_grid(0.01, 0.05, 9), shots=100000, q=0.05,
