@@ -45,8 +45,11 @@ from paper_2609_38139_b300 import inputs as I  # noqa: E402
 METRIC = "shot-ticks/s & msg-updates/s vs HBM/SMEM roofline; batched+lowprec vs plain at equal P_L"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
-# the launch shape is tuned on a whole step when a step has at most this many shots
+# the launch shape is tuned on a whole step when a step has at most this many shots;
+# a larger step is tuned on that many of its shots, each cut at TUNE_TICKS ticks (the
+# rare shots that run a long budget would otherwise decide the sample's time)
 TUNE_MAX_SHOTS = 40000
+TUNE_TICKS = 256
 
 
 def workload(name: str, shots: int, sizes=None, ps=None):
@@ -339,17 +342,28 @@ def main():
         """The arm's parameters with the launch shape lim_autotune picks on a sample
         of this step's points (untimed); the shape never changes results."""
         prm = make_params(prec, variant)
-        if args.block_threads or args.blocks_per_sm or args.smem_cap:
+        if args.block_threads or args.blocks_per_sm or args.smem_cap or (variant or args.variant) != "auto":
             return prm, "given"
-        if args.no_autotune or args.shots * len(pts) > TUNE_MAX_SHOTS:
+        if args.no_autotune:
             return prm, "library default"
-        # tuned on the step itself: every shape times the shots of step 0 to the end
-        best, rate = L.autotune(ctx, step_points(0), prm, sample_shots=args.shots, sample_ticks=0)
+        if args.shots * len(pts) <= TUNE_MAX_SHOTS:
+            # tuned on the step itself: every shape times the shots of step 0 to the end
+            best, rate = L.autotune(ctx, step_points(0), prm, sample_shots=args.shots, sample_ticks=0)
+            sample = "the shots of step 0, run to the end, once per shape (untimed)"
+        else:
+            # one shot per lane needs many shots per lane to pay off, which a sample
+            # this size does not have: a step the library runs that way keeps it
+            if L.plan_describe(ctx, step_points(0), prm)[0]["variant"] == "lane":
+                return prm, "library default (one shot per lane)"
+            n = max(1, TUNE_MAX_SHOTS // len(pts))
+            best, rate = L.autotune(ctx, step_points(0, n), prm, sample_shots=n, sample_ticks=TUNE_TICKS)
+            sample = (f"the first {n} shots of every point of step 0, each cut at {TUNE_TICKS} ticks, "
+                      "once per shape (untimed)")
         best.profile = prm.profile
         return best, {"tuned_by": "lim_autotune", "variant": {v: k for k, v in L.VARIANT.items()}[int(best.variant)],
                       "block_threads": int(best.block_threads), "blocks_per_sm": int(best.blocks_per_sm),
                       "smem_cap": int(best.smem_cap), "tuning_rate_shot_ticks_per_s": rate,
-                      "sample": "the shots of step 0, run to the end, once per shape (untimed)"}
+                      "sample": sample}
 
     prm = make_params(args.precision)
 

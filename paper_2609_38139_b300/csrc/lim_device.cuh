@@ -745,9 +745,13 @@ __device__ __noinline__ void fused_run(int rank, int size, const DevCode &C, con
     CVn = reinterpret_cast<T *>(lim_dyn_smem + (reinterpret_cast<uint8_t *>(CVn) - lim_dyn_smem));
   }
   constexpr int NP = DC * (DV - 1);
-  // checks in flight per thread: wide rows (BB, membrane: 12 gathered values)
-  // one at a time, which keeps the warp-team kernel's spills down (BB +11 %)
-  constexpr int NB = SMEM ? (NP <= 6 ? 2 : 1) : (NP <= 4 ? 4 : (NP <= 6 ? 2 : 1));
+  // checks in flight per thread, as many as the 64 registers of the team kernels
+  // hold without spilling: the global-memory sweeps wait on the latency of their
+  // gathers (3D point rows of six: three checks, +7 % over two; membrane rows of
+  // four qubits in four checks: two, +7 % over one); the bivariate-bicycle rows
+  // (12 gathered values, warp teams) one at a time, which keeps spills down (+11 %)
+  constexpr int NB = SMEM ? (NP <= 6 ? 2 : 1)
+                        : (NP <= 4 ? 4 : (NP <= 6 ? (RULE == LIM_RULE_MINSUM ? 3 : 2) : (DC == 4 ? 2 : 1)));
   if (work && (!SMEM || C.m >= 2 * size)) fused_loop_dyn<PREC, RULE, DC, DV, NB>(work, C, P, sbit, CVp, CVn);
   else fused_loop<PREC, RULE, DC, DV, NB>(rank, size, C, P, sbit, CVp, CVn);
 }

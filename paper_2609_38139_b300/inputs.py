@@ -396,7 +396,10 @@ def p_grid(lo: float, hi: float, npts: int) -> List[float]:
 # ``bench_shots``: shots per point in one benchmark step (default 32), enough to
 # keep every team of the GPU busy through the uneven termination of the shots (the
 # 2D sweep: at 32 per point a step ends with a second wave of the longest L = 128
-# shots on a few teams; from 128 per point the rate is that of larger batches).
+# shots on a few teams; from 128 per point the rate is that of larger batches.
+# The membrane sector: a few shots per 10^4 run the whole 10^4-tick budget, each
+# on one team, so a step of 2048 per point ends with one or two such shots and the
+# rest of the GPU idle -- half the rate of 32768 per point).
 WORKLOADS = {
     # 2D toric code L=8, p=0.05, 1000 shots, tick budget 4L; min-sum FP32.
     "toric2d_L8_small": dict(family="toric2d", sizes=[8], p=[0.05], shots=1000, bench_shots=1000,
@@ -414,12 +417,12 @@ WORKLOADS = {
     "toric3d_point_sweep": dict(family="toric3d_point", sizes=[8, 12, 16, 24],
                                 p=p_grid(0.01, 0.05, 9), shots=100000, q=0.05,
                                 clamp=1000.0, tau=0.1, dt_tick=0.1, K=1, budget="40L",
-                                bench_shots=64),
+                                bench_shots=256),
     # 3D toric membrane-like sector, int16 quantised min-sum.
     "toric3d_membrane_sweep": dict(family="toric3d_membrane", sizes=[6, 8, 12, 16],
                                    p=p_grid(0.01, 0.06, 9), shots=100000, q=0.125,
                                    clamp=1000.0, tau=0.1, dt_tick=0.1, K=1, budget=10000,
-                                   bench_shots=2048),
+                                   bench_shots=32768),
     # bivariate-bicycle codes, int8 quantised min-sum, 1e6 shots mixed over 27 points.
     "bb_mixed": dict(family="bb", sizes=[(6, 6), (15, 3), (12, 6)], p=p_grid(0.01, 0.08, 9),
                      shots=1000000 // 27, q=0.05, clamp=1000.0, tau=0.1, dt_tick=0.1, K=1,
