@@ -448,9 +448,10 @@ def main():
         new one)."""
         bpm = L.MSG_BYTES[prec]
         _, sm = L.plan_describe(ctx, step_points(0), arm_prm)
+        # this rank's launches (the roofline is per GPU): its own tallies
         upd_pt = np.sum([a["msg_updates"] for a in arm["tallies"]], axis=0).astype(np.float64)
-        b_smem = float(upd_pt[sm].sum()) * 2 * bpm / world
-        b_glob = float(upd_pt[~sm].sum()) * 2 * bpm / world
+        b_smem = float(upd_pt[sm].sum()) * 2 * bpm
+        b_glob = float(upd_pt[~sm].sum()) * 2 * bpm
         sec = tot_ms / 1000.0
         cls = {"smem": {"bytes_per_launch": b_smem / args.steps, "achieved_gbs": b_smem / sec / 1e9,
                         "peak_gbs": smem_copy_gbs, "frac": b_smem / sec / 1e9 / smem_copy_gbs,
@@ -593,7 +594,10 @@ def main():
             tt = torch.tensor([e_dt], dtype=torch.float64, device=torch.device("cuda", local))
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             e_dt = float(tt.item())
-        line["e2e"] = {"value": e_ticks / e_dt * world, "unit": "shot-ticks/s",
+            tk = torch.tensor([e_ticks], dtype=torch.float64, device=torch.device("cuda", local))
+            dist.all_reduce(tk, op=dist.ReduceOp.SUM)
+            e_ticks = int(tk.item())
+        line["e2e"] = {"value": e_ticks / e_dt, "unit": "shot-ticks/s",
                        "h2d_bytes_per_step": hb.h2d_bytes(),
                        "d2h_bytes_per_step": hb.d2h_bytes(),
                        "note": "lim_run_batch_host per step: initial errors of the step's shots "
