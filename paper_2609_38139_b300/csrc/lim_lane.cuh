@@ -126,9 +126,27 @@ __device__ __forceinline__ void lane_feedback(const LaunchArgs &A, const DevCode
   int ncand = 0;
   bool overflow = false;
   // pass 1: which active checks ring (the ring-test word of each one's draw),
-  // two draws per step; the ring set goes to s0 (a lane's ring count is small,
-  // so pass 2 runs few, mostly converged, steps)
+  // two draws per step; the ring set goes to s0, and the first kCand ringing
+  // checks keep their draws' priority and tie-break words in registers, so that
+  // pass 2 does not draw them again
   int nring = 0;
+  int rc[kCand];
+  uint32_t ry[kCand], rz[kCand];
+#pragma unroll
+  for (int i = 0; i < kCand; i++) {
+    rc[i] = 0;
+    ry[i] = rz[i] = 0;
+  }
+  auto keep = [&](int c, const U4 &u) {
+#pragma unroll
+    for (int i = 0; i < kCand; i++)
+      if (i == nring) {
+        rc[i] = c;
+        ry[i] = u.y;
+        rz[i] = u.z;
+      }
+    nring++;
+  };
   for (int w = 0; w < C.mw; w++) {
     uint32_t bits = Mm.s[w * 32 + lane], ring = 0;
     while (bits) {
@@ -140,33 +158,34 @@ __device__ __forceinline__ void lane_feedback(const LaunchArgs &A, const DevCode
                                   P.seed_lo, P.seed_hi);
       const U4 u2 = philox4x32_10(S.shot, (uint32_t)S.t, (uint32_t)(32 * w + (b2 < 0 ? b1 : b2)),
                                   (S.pid << 4) | 1u, P.seed_lo, P.seed_hi);
-      if ((uint64_t)u1.x < P.ring_thr) ring |= 1u << b1;
-      if (b2 >= 0 && (uint64_t)u2.x < P.ring_thr) ring |= 1u << b2;
+      if ((uint64_t)u1.x < P.ring_thr) {
+        ring |= 1u << b1;
+        keep(32 * w + b1, u1);
+      }
+      if (b2 >= 0 && (uint64_t)u2.x < P.ring_thr) {
+        ring |= 1u << b2;
+        keep(32 * w + b2, u2);
+      }
     }
     Mm.s0[w * 32 + lane] = ring;
-    nring += __popc(ring);
   }
   // pass 2: Evidence and targets of the ringing checks (Algorithm 1)
   if (nring > kCand) {
     overflow = true;
   } else {
-    for (int w = 0; w < C.mw; w++) {
-      uint32_t ring = Mm.s0[w * 32 + lane];
-      while (ring) {
-        const int c = 32 * w + __ffs(ring) - 1;
-        ring &= ring - 1;
-        const U4 u = philox4x32_10(S.shot, (uint32_t)S.t, (uint32_t)c, (S.pid << 4) | 1u, P.seed_lo, P.seed_hi);
-        const int v = lane_target<PREC, DC, DV>(C, P, CV, zero_msgs, lane, c, u.z);
-        if (v < 0) continue;
-        const uint64_t k = ((uint64_t)u.y << 32) | (uint32_t)c;
 #pragma unroll
-        for (int i = 0; i < kCand; i++)
-          if (i == ncand) {
-            key[i] = k;
-            tgt[i] = v;
-          }
-        ncand++;
-      }
+    for (int j = 0; j < kCand; j++) {
+      if (j >= nring) break;
+      const int v = lane_target<PREC, DC, DV>(C, P, CV, zero_msgs, lane, rc[j], rz[j]);
+      if (v < 0) continue;
+      const uint64_t k = ((uint64_t)ry[j] << 32) | (uint32_t)rc[j];
+#pragma unroll
+      for (int i = 0; i < kCand; i++)
+        if (i == ncand) {
+          key[i] = k;
+          tgt[i] = v;
+        }
+      ncand++;
     }
   }
   if (!overflow) {
