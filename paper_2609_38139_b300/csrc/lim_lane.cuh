@@ -23,7 +23,7 @@ namespace lim {
 namespace lane_detail {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kCand = 4;    // ring candidates of a tick held in registers (more: slow path)
+constexpr int kCand = 8;    // ring candidates of a tick held in registers (more: slow path)
 constexpr int kChunk = 32;  // items a warp takes from its code's queue at once
 
 // One lane's shot.
@@ -94,13 +94,13 @@ __device__ __forceinline__ int lane_target(const DevCode &C, const DevParams &P,
   return vstar;
 }
 
-template <class Key>
-__device__ __forceinline__ void cswap(Key &ka, int &ga, Key &kb, int &gb) {
+template <class Key, class Val>
+__device__ __forceinline__ void cswap(Key &ka, Val &ga, Key &kb, Val &gb) {
   if (kb < ka) {
     const Key k = ka;
     ka = kb;
     kb = k;
-    const int g = ga;
+    const Val g = ga;
     ga = gb;
     gb = g;
   }
@@ -189,11 +189,12 @@ __device__ __forceinline__ void lane_feedback(const LaunchArgs &A, const DevCode
     }
   }
   if (!overflow) {
-    cswap(key[0], tgt[0], key[1], tgt[1]);
-    cswap(key[2], tgt[2], key[3], tgt[3]);
-    cswap(key[0], tgt[0], key[2], tgt[2]);
-    cswap(key[1], tgt[1], key[3], tgt[3]);
-    cswap(key[1], tgt[1], key[2], tgt[2]);
+    // Batcher's odd-even merge sort of eight (19 comparators); empty slots
+    // carry the largest key
+    constexpr int kNet[19][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3}, {4, 6}, {5, 7}, {1, 2}, {5, 6},
+                                 {0, 4}, {1, 5}, {2, 6}, {3, 7}, {2, 4}, {3, 5}, {1, 2}, {3, 4}, {5, 6}};
+#pragma unroll
+    for (int q = 0; q < 19; q++) cswap(key[kNet[q][0]], tgt[kNet[q][0]], key[kNet[q][1]], tgt[kNet[q][1]]);
 #pragma unroll
     for (int i = 0; i < kCand; i++) {
       if (i < ncand) {
@@ -203,13 +204,19 @@ __device__ __forceinline__ void lane_feedback(const LaunchArgs &A, const DevCode
     }
     return;
   }
-  // More ringing checks than registers hold: take them one at a time in
-  // ring-time order from the tick's ring set (s0).
+  // More ringing checks than registers hold: take them in ring-time order, the
+  // next kCand of them per pass over the tick's ring set (s0), kept sorted in
+  // registers as the pass draws them.
   uint64_t last = 0;
   bool first = true;
   for (;;) {
-    uint64_t best = ~0ull;
-    uint32_t best_pick = 0;
+    uint64_t bk[kCand];
+    uint32_t bp[kCand];
+#pragma unroll
+    for (int i = 0; i < kCand; i++) {
+      bk[i] = ~0ull;
+      bp[i] = 0;
+    }
     for (int w = 0; w < C.mw; w++) {
       uint32_t bits = Mm.s0[w * 32 + lane];
       while (bits) {
@@ -217,19 +224,25 @@ __device__ __forceinline__ void lane_feedback(const LaunchArgs &A, const DevCode
         bits &= bits - 1;
         const U4 u = philox4x32_10(S.shot, (uint32_t)S.t, (uint32_t)c, (S.pid << 4) | 1u, P.seed_lo, P.seed_hi);
         const uint64_t k = ((uint64_t)u.y << 32) | (uint32_t)c;
-        if ((first || k > last) && k < best) {
-          best = k;
-          best_pick = u.z;
+        if ((first || k > last) && k < bk[kCand - 1]) {
+          bk[kCand - 1] = k;
+          bp[kCand - 1] = u.z;
+#pragma unroll
+          for (int i = kCand - 1; i > 0; i--) cswap(bk[i - 1], bp[i - 1], bk[i], bp[i]);
         }
       }
     }
-    if (best == ~0ull) break;
+    if (bk[0] == ~0ull) break;
     first = false;
-    last = best;
-    const int c = (int)(uint32_t)best;
-    if (!((Mm.s[(c >> 5) * 32 + lane] >> (c & 31)) & 1)) continue;  // cleared by an earlier move
-    const int v = lane_target<PREC, DC, DV>(C, P, CV, zero_msgs, lane, c, best_pick);
-    if (v >= 0) lane_flip<DC, DV>(C, Mm.e, Mm.s, lane, v, S);
+#pragma unroll
+    for (int i = 0; i < kCand; i++) {
+      if (bk[i] == ~0ull) break;
+      last = bk[i];
+      const int c = (int)(uint32_t)bk[i];
+      if (!((Mm.s[(c >> 5) * 32 + lane] >> (c & 31)) & 1)) continue;  // cleared by an earlier move
+      const int v = lane_target<PREC, DC, DV>(C, P, CV, zero_msgs, lane, c, bp[i]);
+      if (v >= 0) lane_flip<DC, DV>(C, Mm.e, Mm.s, lane, v, S);
+    }
   }
 }
 
@@ -291,7 +304,6 @@ template <int PREC, int RULE, int DC, int DV>
 __device__ __forceinline__ void lane_sweep(const DevCode &C, const DevParams &P, const LaneMem<typename MT<PREC>::T> &Mm,
                                            int sel, int lane, int lane_sweeps) {
   using T = typename MT<PREC>::T;
-  constexpr int NP = DC * (DV - 1);
   constexpr int NB = 4;  // checks per group (divides 32)
   const T *CVp = Mm.buf((sel + 2) % 3);
   T *CVn = Mm.buf((sel + 1) % 3);

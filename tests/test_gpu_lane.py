@@ -83,8 +83,12 @@ def test_lane_kernel_against_oracle(L, ctx, cid, maker, prec, qs, q, rule, p, T,
     conv = ora["converged"] == 1
     assert tal[0]["sum_t"] == int(ora["t_clr"][conv].sum())
     if ring == 1.0:
-        # many active checks ring together: ticks with more than four candidates
-        # take the ordered slow path; the trajectories above went through it
+        # every active check rings: the first tick of a shot with more than eight
+        # defects has more candidates than the registers hold and takes the
+        # ordered passes over the ring set; the trajectories above went through it
+        _, s0 = L.sample_noise(lc, p, 21, 3, 0, shots)
+        defects = L.bits_to_bytes(s0.cpu().numpy(), code.m).sum(axis=1)
+        assert int((defects > 8).sum()) > shots // 4
         assert int(ora["moves"].sum()) > 4 * shots
 
 
