@@ -4,9 +4,10 @@
 Workload (default): the batched 2D toric sweep -- L in {16, 32, 64, 128}, 11
 error rates p in 0.02..0.12, FP32 min-sum, check-centric feedback, one BP
 sweep per tick (dt = tau = 0.1), tick budget 40L, all points mixed in one
-persistent launch.  One step = one lim_run_batch over ``--shots`` fresh shots
-of every point (a sample of the configuration's 10^5 per point), run to
-completion.
+persistent launch.  One step = one persistent launch over ``--shots`` fresh
+shots of every point (a sample of the configuration's 10^5 per point), run to
+completion: the batch is captured once as a CUDA graph (lim_graph_create) and
+each step replays it on its own window of shot ids (lim_graph_launch).
 
 Prints one JSON line.  ``value`` is shot-ticks per second of the main arm
 (ticks executed, summed over shots, divided by the device time of the steps).
@@ -382,16 +383,18 @@ def main():
     def timed_arm(arm_prm):
         """W untimed and K timed steps of one storage precision: device times of the
         steps (CUDA events on the launching stream), their tallies, and the step-0
-        records (for the paired comparisons)."""
+        records (for the paired comparisons).  The step's batch is captured once as
+        a CUDA graph (queue reset, tally reset, the persistent kernel) and every
+        step replays it on its own window of shot ids."""
         batch = L.Batch(ctx, step_points(0), arm_prm, records=True)
+        batch.capture()
 
         def run_step(step, timed_events=None):
-            batch.points = step_points(step)
-            batch.pts = L._points(batch.points)
             flush.fill_(step & 0xFF)  # evict L2 between steps (outside the timed window)
             if timed_events:
                 timed_events[0].record(stream)
-            batch.run(0, stream)
+            # step_points(step) = step_points(0) shifted by step * world * shots
+            batch.replay(0, step * world * args.shots, stream)
             if timed_events:
                 timed_events[1].record(stream)
 
@@ -485,7 +488,8 @@ def main():
                            parallelism=f"replicas x{world}, disjoint shot ids",
                            launch_shape=tuned),
             "sample": f"{args.shots} fresh shot ids of every point per step "
-                      f"({args.shots * len(pts)} shots per launch, one launch per step)",
+                      f"({args.shots * len(pts)} shots per launch, one launch per step: a replay of "
+                      "the batch captured once as a CUDA graph, lim_graph_launch)",
             "ms_steps": [round(x, 3) for x in main_arm["ms_steps"]],
             "msg_updates_per_s": upd / (tot_ms / 1000.0),
             "ler_sample": fails / max(1, shots),

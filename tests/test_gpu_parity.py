@@ -571,12 +571,14 @@ def test_plain_path_equals_batched_kernel(L, ctx, rule, fb):
         compare_records(rec_p[:50], ora, "plain")
 
 
-def test_graph_replay_equals_run_batch(L, ctx):
+@pytest.mark.parametrize("variant", ["auto", "cta", "warp", "lane"])
+def test_graph_replay_equals_run_batch(L, ctx, variant):
     """A batch captured as a CUDA graph and replayed with new seeds and shot
-    windows gives exactly the results of direct lim_run_batch calls."""
+    windows gives exactly the results of direct lim_run_batch calls, for every
+    launch kind (the lane kernel's per-code queues included)."""
     c8 = ctx.from_inputs(I.toric2d(8))
     bb = ctx.from_inputs(I.bb_code(6, 6))
-    prm = L.params(precision="f32", tick_budget=40)
+    prm = L.params(precision="f32", tick_budget=40, variant=variant)
     pts = [(c8, 0.05, 64, 10, 0), (bb, 0.04, 64, 10, 1)]
     b = L.Batch(ctx, pts, prm)
     b.capture()
