@@ -14,6 +14,7 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
+import threading
 from concurrent.futures import ThreadPoolExecutor
 from typing import Optional
 
@@ -29,14 +30,21 @@ FEEDBACK = {"check_move": 0, "bit_discrete": 1, "check_move_multi": 2}
 PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "i16": 4, "i8": 5}
 
 
+# the shot runners call lib() from several threads at once: the first call builds
+# and loads the library, the others wait for it
+_build_lock = threading.Lock()
+_load_lock = threading.Lock()
+
+
 def build(force: bool = False) -> str:
-    stale = (not os.path.exists(_LIB) or
-             os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
-    if force or stale:
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off",
-                               "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+    with _build_lock:
+        stale = (not os.path.exists(_LIB) or
+                 os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+        if force or stale:
+            tmp = _LIB + f".tmp{os.getpid()}.{threading.get_ident()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off",
+                                   "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, _LIB)
     return _LIB
 
 
@@ -84,37 +92,39 @@ _lib: Optional[ctypes.CDLL] = None
 def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        L = _lib
-        vp = ctypes.c_void_p
-        L.or_philox4x32_10.argtypes = [vp, vp, vp]
-        L.or_philox4x64_10.argtypes = [vp, vp, vp]
-        L.or_noise.argtypes = [ctypes.POINTER(Code), ctypes.c_double, ctypes.c_uint64,
-                               ctypes.c_uint32, ctypes.c_uint32, vp, vp]
-        L.or_run_shot.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), ctypes.c_double,
-                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
-                                  ctypes.POINTER(Record), ctypes.POINTER(Trace)]
-        L.or_run_from.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), vp,
-                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
-                                  ctypes.POINTER(Record), ctypes.POINTER(Trace)]
-        L.or_run_shots.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), ctypes.c_double,
-                                   ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
-                                   ctypes.c_uint32, vp]
-        L.or_multi_move_set.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
-        L.or_multi_move_set.restype = ctypes.c_uint32
-        L.or_bp_decode.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), ctypes.c_double,
-                                   ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
-                                   ctypes.POINTER(Record), vp]
-        L.or_bp_sweeps.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), vp, vp, vp, vp,
-                                   vp, vp, ctypes.c_int32]
-        L.or_readout.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), vp, vp, vp]
-        L.or_derive.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Derived)]
-        L.or_theta.argtypes = [ctypes.POINTER(Params), ctypes.c_int32]
-        L.or_theta.restype = ctypes.c_double
-        L.or_round_f16.argtypes = [ctypes.c_double]
-        L.or_round_f16.restype = ctypes.c_double
-        L.or_round_bf16.argtypes = [ctypes.c_double]
-        L.or_round_bf16.restype = ctypes.c_double
+        with _load_lock:
+            if _lib is None:
+                L = ctypes.CDLL(build())
+                vp = ctypes.c_void_p
+                L.or_philox4x32_10.argtypes = [vp, vp, vp]
+                L.or_philox4x64_10.argtypes = [vp, vp, vp]
+                L.or_noise.argtypes = [ctypes.POINTER(Code), ctypes.c_double, ctypes.c_uint64,
+                                       ctypes.c_uint32, ctypes.c_uint32, vp, vp]
+                L.or_run_shot.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), ctypes.c_double,
+                                          ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                          ctypes.POINTER(Record), ctypes.POINTER(Trace)]
+                L.or_run_from.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), vp,
+                                          ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                          ctypes.POINTER(Record), ctypes.POINTER(Trace)]
+                L.or_run_shots.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), ctypes.c_double,
+                                           ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                           ctypes.c_uint32, vp]
+                L.or_multi_move_set.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+                L.or_multi_move_set.restype = ctypes.c_uint32
+                L.or_bp_decode.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), ctypes.c_double,
+                                           ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                           ctypes.POINTER(Record), vp]
+                L.or_bp_sweeps.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), vp, vp, vp, vp,
+                                           vp, vp, ctypes.c_int32]
+                L.or_readout.argtypes = [ctypes.POINTER(Code), ctypes.POINTER(Params), vp, vp, vp]
+                L.or_derive.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Derived)]
+                L.or_theta.argtypes = [ctypes.POINTER(Params), ctypes.c_int32]
+                L.or_theta.restype = ctypes.c_double
+                L.or_round_f16.argtypes = [ctypes.c_double]
+                L.or_round_f16.restype = ctypes.c_double
+                L.or_round_bf16.argtypes = [ctypes.c_double]
+                L.or_round_bf16.restype = ctypes.c_double
+                _lib = L  # published only once every signature is set
     return _lib
 
 
