@@ -969,6 +969,7 @@ int lim_autotune(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_pa
     const Shape shapes[] = {{LIM_VARIANT_CTA, 1024, 1, 0},        {LIM_VARIANT_CTA, 1024, 1, -1},
                             {LIM_VARIANT_CTA, 1024, 1, 48 << 10}, {LIM_VARIANT_CTA, 512, 2, 0},
                             {LIM_VARIANT_CTA, 512, 1, 0},         {LIM_VARIANT_CTA, 256, 4, 0},
+                            {LIM_VARIANT_CTA, 192, 5, 0},
                             {LIM_VARIANT_WARP, 256, 0, 0},        {LIM_VARIANT_WARP, 512, 0, 0},
                             {LIM_VARIANT_WARP, 128, 0, 0},        {LIM_VARIANT_LANE, 128, 0, 0},
                             {LIM_VARIANT_LANE, 64, 0, 0},         {LIM_VARIANT_LANE, 32, 0, 0}};

@@ -406,7 +406,7 @@ def test_mixed_batch_and_launch_shape_invariance(L, ctx):
         ora = oracle_point(code, prm, p, 3, pid_, s0, n)
         compare_records(rec[off:off + n], ora, f"{code.name} p={p}")
         off += n
-    for variant, bt in (("cta", 128), ("warp", 64), ("warp", 512)):
+    for variant, bt in (("cta", 128), ("cta", 192), ("warp", 64), ("warp", 512)):
         prm2 = L.params(precision="i8", quant_scale=0.25, tick_budget=300, variant=variant,
                         block_threads=bt)
         _, rec2 = L.run_batch(ctx, pts, prm2, 3)
