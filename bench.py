@@ -464,7 +464,9 @@ def main():
                           "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}}
         dom = "smem" if b_smem / smem_copy_gbs > b_glob / hbm else "global"
         c = cls[dom]
-        traffic = measured_traffic(args.workload, prec, (b_smem + b_glob) / args.steps)
+        # the records are of the workload's own rule, feedback and sweeps per tick
+        own = not (args.rule or args.feedback or args.sweeps_per_tick > 0 or sizes or ps)
+        traffic = measured_traffic(args.workload, prec, (b_smem + b_glob) / args.steps) if own else None
         out = {"bound": "smem" if dom == "smem" else "hbm", "achieved": c["achieved_gbs"],
                "peak": c["peak_gbs"], "unit": "GB/s", "frac": c["frac"], "traffic": traffic,
                "kernel": "batch_kernel (persistent)",
