@@ -235,13 +235,16 @@ def run_reference(args):
         w["K"] = args.sweeps_per_tick
     npts = len(I.workload_points(args.workload))
     steps = []
+    # each step a bounded sample: about --ref-seconds, less when many steps are asked
+    # for, so that the whole run stays within a few minutes
+    per_step = min(args.ref_seconds, max(2.0, 150.0 / max(1, args.steps)))
     for _ in range(args.warmup):
-        cpu_baseline(args.workload, args.precision, seconds=max(1.0, args.ref_seconds / 4),
+        cpu_baseline(args.workload, args.precision, seconds=max(1.0, per_step / 4),
                      rule=args.rule, sweeps=args.sweeps_per_tick, feedback=args.feedback)
     t0 = time.perf_counter()
     last = None
     for _ in range(args.steps):
-        last = cpu_baseline(args.workload, args.precision, seconds=args.ref_seconds, rule=args.rule,
+        last = cpu_baseline(args.workload, args.precision, seconds=per_step, rule=args.rule,
                             sweeps=args.sweeps_per_tick, feedback=args.feedback)
         steps.append(last)
     wall = time.perf_counter() - t0
