@@ -60,7 +60,7 @@ class Params(ctypes.Structure):
                 ("q", ctypes.c_double), ("clamp", ctypes.c_double), ("tau", ctypes.c_double),
                 ("dt_tick", ctypes.c_double), ("sweeps_per_tick", ctypes.c_int32),
                 ("ring_prob", ctypes.c_double), ("tick_budget", ctypes.c_int32),
-                ("gauge_on_move", ctypes.c_int32)]
+                ("gauge_on_move", ctypes.c_int32), ("tie_rel", ctypes.c_double)]
 
 
 class Record(ctypes.Structure):
@@ -152,10 +152,10 @@ class OracleCode:
 
 def params(rule="minsum", feedback="check_move", precision="f64", quant_scale=2.0 ** -6,
            q=0.05, clamp=1000.0, tau=0.1, dt_tick=0.1, sweeps_per_tick=1, ring_prob=-1.0,
-           tick_budget=32, gauge_on_move=0) -> Params:
+           tick_budget=32, gauge_on_move=0, tie_rel=0.0) -> Params:
     return Params(RULE[rule], FEEDBACK[feedback], PREC[precision], float(quant_scale), float(q),
                   float(clamp), float(tau), float(dt_tick), int(sweeps_per_tick), float(ring_prob),
-                  int(tick_budget), int(gauge_on_move))
+                  int(tick_budget), int(gauge_on_move), float(tie_rel))
 
 
 def _check(st: int, what: str):

@@ -134,6 +134,8 @@ static int setup_wk(const or_params *prm, wk *w) {
   w->is_f32 = (prm->precision == OR_PREC_F32 || prm->precision == OR_PREC_F16 ||
                prm->precision == OR_PREC_BF16);
   if (w->is_int && prm->rule != OR_RULE_MINSUM) return OR_E_UNSUPPORTED;
+  if (!(prm->tie_rel >= 0.0 && prm->tie_rel <= 0.5)) return OR_E_INVAL;
+  if (w->is_int && prm->tie_rel != 0.0) return OR_E_INVAL;
   /* alpha = dt / (K tau): K Euler steps of tau dm/dt = F(m) - m per tick. */
   if (prm->tau > 0.0 && prm->dt_tick > 0.0) {
     w->alpha = prm->dt_tick / (prm->sweeps_per_tick * prm->tau);
@@ -207,6 +209,18 @@ static double w_relax(const wk *w, double m_old, double m_new) {
  * clamped again, then rounded to the storage format. */
 static double w_update(const wk *w, double m_old, double m_raw) {
   return w_store(w, w_clamp(w, w_relax(w, m_old, w_clamp(w, m_raw))));
+}
+
+/* Lower end of LocalMove's tie set (Algorithm 1: the argmax, ties broken
+ * uniformly): best - tie_rel * max(1, |best|).  In the binary32 modes tie_rel is
+ * held as binary32 and the product and the difference are each rounded to
+ * binary32, the arithmetic of the beliefs themselves; integer modes tie exactly
+ * (setup_wk refuses a nonzero tie_rel there). */
+static double tie_floor(const wk *w, double tie_rel, double best) {
+  if (w->is_int || tie_rel == 0.0) return best;
+  const double a = fabs(best) > 1.0 ? fabs(best) : 1.0;
+  if (w->is_f32) return r32(best - r32(r32(tie_rel) * a));
+  return best - tie_rel * a;
 }
 
 double or_theta(const or_params *prm, int32_t d) {
@@ -643,14 +657,16 @@ static int run(const or_code *code, const or_params *prm, double p, const uint8_
           for (int j = 0; j < d; j++)
             if (L[g.cvar[b + j]] > best) best = L[g.cvar[b + j]];
           if (!(best >= theta[d])) continue; /* (ii) Evidence(c) >= 1/d_c */
-          /* LocalMove: flip a qubit of argmax_w Pr_BP(e_w|s), ties broken uniformly. */
+          /* LocalMove: flip a qubit of argmax_w Pr_BP(e_w|s), ties broken uniformly;
+           * the ties are the beliefs >= lo (lo = best when tie_rel = 0). */
+          const double lo = tie_floor(&w, prm->tie_rel, best);
           int nt = 0;
           for (int j = 0; j < d; j++)
-            if (L[g.cvar[b + j]] == best) nt++;
+            if (L[g.cvar[b + j]] >= lo) nt++;
           int pick = (int)(((uint64_t)rings[i].pick * (uint64_t)nt) >> 32);
           int first = -1;
           for (int j = 0; j < d; j++)
-            if (L[g.cvar[b + j]] == best) {
+            if (L[g.cvar[b + j]] >= lo) {
               if (pick == 0) { first = j; break; }
               pick--;
             }

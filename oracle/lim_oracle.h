@@ -92,6 +92,12 @@ typedef struct {
   double ring_prob;        /* < 0: 1 - exp(-dt_tick)                   */
   int32_t tick_budget;     /* T                                        */
   int32_t gauge_on_move;   /* CHECK_MOVE only: gauge-switch the flipped qubit */
+  double tie_rel;          /* LocalMove's argmax ties: every qubit of N(c) whose
+                              belief is >= best - tie_rel * max(1, |best|);
+                              0 = exact equality.  Binary32 emulation modes
+                              hold tie_rel as binary32 and round the product
+                              and the difference to binary32.  Floating modes
+                              only (integer modes: 0); 0 <= tie_rel <= 0.5.  */
 } or_params;
 
 typedef struct {
