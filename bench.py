@@ -75,7 +75,7 @@ def lib_params(L, w, name, prec, variant="auto"):
                     precision=prec, quant_scale=qs,
                     q=w["q"], clamp=w["clamp"], tau=w["tau"],
                     dt_tick=w["dt_tick"], sweeps_per_tick=w["K"], tick_budget=w.get("T", 0) or 1,
-                    variant=variant)
+                    variant=variant, tie_rel=L.default_tie_rel(prec, w.get("rule", "minsum")))
 
 
 class Clocks:
@@ -155,6 +155,11 @@ def _default_quant_scale(prec: str, q: float) -> float:
     return lim.default_quant_scale(prec, q)
 
 
+def _default_tie_rel(prec: str, rule: str) -> float:
+    from paper_2609_38139_b300 import lim
+    return lim.default_tie_rel(prec, rule)
+
+
 def cpu_baseline(name: str, prec: str, seconds: float = 15.0, threads: int = 0, rule: str = "",
                  sweeps: int = 0, feedback: str = ""):
     """The oracle timed on this host's cores on a bounded sample of the workload:
@@ -193,7 +198,8 @@ def cpu_baseline(name: str, prec: str, seconds: float = 15.0, threads: int = 0, 
                               rule=w.get("rule", "minsum"), feedback=w.get("feedback", "check_move"),
                               quant_scale=_default_quant_scale(prec, w["q"]),
                               q=w["q"], clamp=w["clamp"], tau=w["tau"],
-                              dt_tick=w["dt_tick"], sweeps_per_tick=w["K"], tick_budget=d["T"])
+                              dt_tick=w["dt_tick"], sweeps_per_tick=w["K"], tick_budget=d["T"],
+                              tie_rel=_default_tie_rel(prec, w.get("rule", "minsum")))
                 futs.append((c, ex.submit(O.run_shots, oc, op, d["p"], 0, d["point_id"], rnd, 1)))
             for c, f in futs:
                 r = f.result()
@@ -298,6 +304,9 @@ def main():
     ap.add_argument("--print-source-hash", action="store_true")
     ap.add_argument("--sizes", default="", help="comma list restricting the code sizes")
     ap.add_argument("--ps", default="", help="comma list restricting the error rates")
+    ap.add_argument("--tie-rel", type=float, default=-1.0,
+                    help="LocalMove tie tolerance of the binary16/bfloat16 arms (default: the "
+                         "library's default for the format; 0: exact ties)")
     args = ap.parse_args()
     if args.print_source_hash:
         print(kernel_source_hash())
@@ -340,6 +349,8 @@ def main():
         prm.blocks_per_sm = args.blocks_per_sm
         prm.profile = 1 if args.phases else 0
         prm.smem_cap = args.smem_cap
+        if args.tie_rel >= 0 and prec in ("f16", "bf16"):
+            prm.tie_rel = args.tie_rel
         return prm
 
     def tuned_params(prec, variant=None):
@@ -526,6 +537,7 @@ def main():
                        "msg_updates_per_s": a_upd / (a_ms / 1000.0),
                        "ler_sample": a_fails / max(1, a_shots),
                        "launch_shape": lp_shape,
+                       "tie_rel": float(lp_prm.tie_rel),
                        "roofline": roofline(arm, lp, a_ms, lp_prm)}
     if lowprec:
         line["lowprec"] = lowprec

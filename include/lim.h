@@ -154,6 +154,19 @@ typedef struct {
                            /* that fits.  A smaller cap leaves more of the SM's      */
                            /* unified L1/shared array to the L1 cache, which serves  */
                            /* the codes whose messages stay in HBM                   */
+  double tie_rel;          /* LocalMove's argmax over N(c) ("ties broken uniformly", */
+                           /* Algorithm 1): the tie set is every qubit whose belief  */
+                           /* is >= best - tie_rel * max(1, |best|), the product and */
+                           /* the difference each rounded to binary32 (tie_rel held  */
+                           /* as binary32).  0 = exact equality.  With alpha = 1,    */
+                           /* exact min-sum beliefs are integer combinations of the  */
+                           /* prior, so distinct beliefs differ by whole prior units */
+                           /* while binary16/bfloat16 message storage turns exact    */
+                           /* ties into near-ties a few storage ulps apart; a small  */
+                           /* tie_rel keeps them ties.  Floating formats only (an    */
+                           /* integer format must give 0); 0 <= tie_rel <= 0.5.      */
+                           /* Check-centric rules only (the bit-centric rule has no  */
+                           /* argmax).                                              */
 } lim_params;
 
 typedef struct {

@@ -77,6 +77,8 @@ int derive(const lim_params *p, DevParams &o) {
   if (!(p->clamp > 0.0)) return bad(LIM_E_INVAL, "clamp must be > 0");
   if (p->sweeps_per_tick < 1) return bad(LIM_E_INVAL, "sweeps_per_tick must be >= 1");
   if (p->tick_budget < 0) return bad(LIM_E_INVAL, "tick_budget must be >= 0");
+  if (!(p->tie_rel >= 0.0 && p->tie_rel <= 0.5)) return bad(LIM_E_INVAL, "tie_rel must be in [0, 0.5]");
+  if (is_int && p->tie_rel != 0.0) return bad(LIM_E_INVAL, "tie_rel must be 0 for integer messages");
   double alpha = 1.0;
   if (p->tau > 0.0 && p->dt_tick > 0.0) alpha = p->dt_tick / (p->sweeps_per_tick * p->tau);
   if (!(alpha > 0.0 && alpha <= 1.0)) return bad(LIM_E_INVAL, "alpha = dt/(K tau) must be in (0,1]");
@@ -103,6 +105,7 @@ int derive(const lim_params *p, DevParams &o) {
     o.pi_f = (float)pi;
     o.clamp_f = (float)p->clamp;
     o.alpha_f = (float)alpha;
+    o.tie_rel_f = (float)p->tie_rel;
     for (int k = 0; k <= kMaxDeg; k++)
       o.theta_f[k] = k <= 1 ? INFINITY : (float)(-std::log((double)(k - 1)));
   }

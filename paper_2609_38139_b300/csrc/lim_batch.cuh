@@ -363,15 +363,16 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
           }
         }
         if (!evidence(P, best, d)) continue;
+        const Acc lo = tie_floor(P, best);
         int nt = 0;
 #pragma unroll
         for (int j = 0; j < kMaxDeg; j++)
-          if (j < d && Lv[j] == best) nt++;
+          if (j < d && Lv[j] >= lo) nt++;
         int pick = (int)(((uint64_t)u.z * (uint64_t)nt) >> 32);
         int vstar = -1, first = -1;
 #pragma unroll
         for (int j = 0; j < kMaxDeg; j++) {
-          if (j < d && Lv[j] == best) {
+          if (j < d && Lv[j] >= lo) {
             if (pick == 0 && vstar < 0) {
               vstar = __ldg(C.c_var + cb + j);
               first = j;
@@ -531,13 +532,14 @@ __device__ bool shot_tick(const Team &tm, const LaunchArgs &A, const DevPoint &p
             if (Lv[j] > best) best = Lv[j];
           }
           if (!evidence(P, best, d)) continue;
+          const Acc lo = tie_floor(P, best);
           int nt = 0;
           for (int j = 0; j < d; j++)
-            if (Lv[j] == best) nt++;
+            if (Lv[j] >= lo) nt++;
           int pick = (int)(((uint64_t)(uint32_t)V.ctgt[c] * (uint64_t)nt) >> 32);
           int first = -1;
           for (int j = 0; j < d; j++)
-            if (Lv[j] == best) {
+            if (Lv[j] >= lo) {
               if (pick == 0) {
                 first = j;
                 break;

@@ -108,6 +108,16 @@ __device__ __forceinline__ bool evidence(const DevParams &P, int32_t best, int d
   return best >= P.theta_q[d];
 }
 
+// Lower end of LocalMove's tie set (argmax, "ties broken uniformly", Algorithm 1):
+// the qubits of N(c) whose belief is >= tie_floor(best).  best - tie_rel *
+// max(1, |best|) with the product and the difference each rounded to binary32
+// (explicit _rn: no contraction into one fused multiply-add); tie_rel = 0 gives
+// best, i.e. exact ties.  Integer steps tie exactly.
+__device__ __forceinline__ float tie_floor(const DevParams &P, float best) {
+  return __fsub_rn(best, __fmul_rn(P.tie_rel_f, fmaxf(1.f, fabsf(best))));
+}
+__device__ __forceinline__ int32_t tie_floor(const DevParams &, int32_t best) { return best; }
+
 // New stored value of a message from its old value and its raw BP value:
 // clamp (Sec. S4), Euler step m + alpha (F - m) of the relaxation ODE
 // (Algorithm 1; skipped when alpha = 1), clamp again; the store rounds.

@@ -59,6 +59,7 @@ struct DevParams {
   int32_t alpha_is_one, profile;
   int32_t multi;                 // check-centric rule with the multi-qubit move
   float pi_f, clamp_f, alpha_f;
+  float tie_rel_f;               // LocalMove tie tolerance (floating formats; 0: exact ties)
   int32_t pi_q, clamp_q, A;
   float theta_f[kMaxDeg + 1];    // evidence threshold by check degree
   int32_t theta_q[kMaxDeg + 1];

@@ -79,14 +79,15 @@ __device__ __forceinline__ int lane_target(const DevCode &C, const DevParams &P,
     best = L > best ? L : best;
   }
   if (!evidence(P, best, DC)) return -1;
+  const A lo = tie_floor(P, best);
   int nt = 0;
 #pragma unroll
-  for (int j = 0; j < DC; j++) nt += Lv[j] == best;
+  for (int j = 0; j < DC; j++) nt += Lv[j] >= lo;
   int pick = (int)(((uint64_t)pick_word * (uint64_t)nt) >> 32);
   int vstar = -1;
 #pragma unroll
   for (int j = 0; j < DC; j++) {
-    if (Lv[j] == best) {
+    if (Lv[j] >= lo) {
       if (pick == 0 && vstar < 0) vstar = __ldg(C.c_var + c * DC + j);
       pick--;
     }

@@ -62,7 +62,8 @@ class Params(ctypes.Structure):
                 ("ring_prob", ctypes.c_double), ("tick_budget", ctypes.c_int32),
                 ("gauge_on_move", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("smem_cap", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("smem_cap", ctypes.c_int32),
+                ("tie_rel", ctypes.c_double)]
 
 
 class Point(ctypes.Structure):
@@ -146,13 +147,31 @@ def check(st: int, what: str = "") -> None:
 def params(rule="minsum", feedback="check_move", precision="f32", quant_scale=2.0 ** -6, q=0.05,
            clamp=1000.0, tau=0.1, dt_tick=0.1, sweeps_per_tick=1, ring_prob=-1.0, tick_budget=32,
            gauge_on_move=0, variant="auto", block_threads=0, blocks_per_sm=0, profile=0,
-           smem_cap=0) -> Params:
+           smem_cap=0, tie_rel=0.0) -> Params:
     if feedback == "bp_decoder":  # ordinary BP decoding is the discrete machine (LIM_FB_BP_DECODER)
         feedback = "bit_discrete"
     return Params(RULE[rule], FEEDBACK[feedback], PREC[precision], float(quant_scale), float(q),
                   float(clamp), float(tau), float(dt_tick), int(sweeps_per_tick), float(ring_prob),
                   int(tick_budget), int(gauge_on_move), VARIANT[variant], int(block_threads),
-                  int(blocks_per_sm), int(profile), int(smem_cap))
+                  int(blocks_per_sm), int(profile), int(smem_cap), float(tie_rel))
+
+
+def default_tie_rel(precision: str, rule: str = "minsum") -> float:
+    """Default LocalMove tie tolerance (``lim_params.tie_rel``) of a storage format.
+
+    With alpha = 1 the exact min-sum beliefs are integer combinations of the
+    prior (and of CLAMP), so beliefs that differ at all differ by about a prior
+    unit, and the exact ties among the beliefs of a check are frequent; LocalMove
+    breaks them uniformly at random (Algorithm 1).  Binary16 and bfloat16 storage
+    rounds the messages, which turns those ties into near-ties a few storage ulps
+    apart that the argmax would break by rounding noise.  A tie set of every
+    belief within 2^-5 (binary16, 11-bit significand) or 2^-4 (bfloat16, 8-bit)
+    of max(1, |best|) keeps them ties: the trajectories then reproduce FP64's
+    failures.  0 (exact ties) for FP32, the integer formats (exact on their
+    lattice) and the sum-product rule."""
+    if rule != "minsum":
+        return 0.0
+    return {"f16": 2.0 ** -5, "bf16": 2.0 ** -4}.get(precision, 0.0)
 
 
 def default_quant_scale(precision: str, q: float) -> float:

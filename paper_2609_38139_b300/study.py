@@ -36,7 +36,8 @@ def workload_params(w: dict, precision: str = "f32", rule: str = "", feedback: s
     return lim.params(rule=rule, feedback=feedback or w.get("feedback", "check_move"),
                       precision=precision,
                       quant_scale=qs, q=w["q"], clamp=w["clamp"], tau=w["tau"],
-                      dt_tick=w["dt_tick"], sweeps_per_tick=w["K"], tick_budget=1)
+                      dt_tick=w["dt_tick"], sweeps_per_tick=w["K"], tick_budget=1,
+                      tie_rel=lim.default_tie_rel(precision, rule))
 
 
 def point_stats(t: np.void, dt_tick: float) -> Dict[str, float]:

@@ -18,7 +18,8 @@ def oracle_params(prm, precision=None):
     return O.params(rule=rule, feedback=fb, precision=prec, quant_scale=prm.quant_scale, q=prm.q,
                     clamp=prm.clamp, tau=prm.tau, dt_tick=prm.dt_tick,
                     sweeps_per_tick=prm.sweeps_per_tick, ring_prob=prm.ring_prob,
-                    tick_budget=prm.tick_budget, gauge_on_move=prm.gauge_on_move)
+                    tick_budget=prm.tick_budget, gauge_on_move=prm.gauge_on_move,
+                    tie_rel=prm.tie_rel)
 
 
 def oracle_point(code, prm, p, seed, point_id, shot0, nshots, tick_budget=0, precision=None):

@@ -123,6 +123,14 @@ def test_params_check(L):
         L.params_check(L.params(tau=0.1, dt_tick=0.5))  # alpha > 1
     with pytest.raises(L.LimError, match="LIM_E_INVAL"):
         L.params_check(L.params(sweeps_per_tick=0))
+    # LocalMove tie tolerance: floating formats, 0 <= tie_rel <= 0.5
+    L.params_check(L.params(precision="f16", tie_rel=2.0 ** -5))
+    L.params_check(L.params(precision="bf16", tie_rel=0.5))
+    for bad in (-2.0 ** -5, 0.75, float("nan")):
+        with pytest.raises(L.LimError, match="LIM_E_INVAL"):
+            L.params_check(L.params(precision="f16", tie_rel=bad))
+    with pytest.raises(L.LimError, match="LIM_E_INVAL"):
+        L.params_check(L.params(precision="i16", tie_rel=2.0 ** -5))
 
 
 def test_host_context_refuses_compute(L, host):

@@ -4,7 +4,9 @@ workload's code sizes in one launch, so the shared-memory plan -- which codes
 keep their messages in shared memory and which stream them from global memory
 -- is the benchmark's), against the oracle shot by shot in the same precision.
 Every integer result (t_clr, converged, failed, moves, ticks, sweeps) and the
-final residual of each sampled shot is bit-exact.
+final residual of each sampled shot is bit-exact.  Binary16 and bfloat16 run
+with the library's default LocalMove tie tolerance of their format, as the
+benchmark does.
 """
 import numpy as np
 import pytest
@@ -41,7 +43,8 @@ def _workload_sample(L, ctx, workload, prec, picks, seed=0, shot0=7000):
     qs = L.default_quant_scale(prec, w["q"])
     prm = L.params(rule=w.get("rule", "minsum"), feedback=w.get("feedback", "check_move"),
                    precision=prec, quant_scale=qs, q=w["q"], clamp=w["clamp"], tau=w["tau"],
-                   dt_tick=w["dt_tick"], sweeps_per_tick=w["K"], tick_budget=1)
+                   dt_tick=w["dt_tick"], sweeps_per_tick=w["K"], tick_budget=1,
+                   tie_rel=L.default_tie_rel(prec, w.get("rule", "minsum")))
     pts, meta = [], []
     pid = 0
     for size in w["sizes"]:

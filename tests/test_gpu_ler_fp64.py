@@ -18,7 +18,10 @@ turn exact ties into near-ties that the argmax then breaks by rounding noise
 instead of by the random pick: on large samples their logical error rate is
 lower than FP64's by 5-15 %, beyond 3 sigma.  So is int8's with Delta = 2^-2,
 whose messages saturate at 127 steps = 31.75 LLR instead of CLAMP = 1000.
-Those tests state the target and are marked as expected failures.
+Those tests state the target and are marked as expected failures: they run
+binary16 and bfloat16 with exact ties (tie_rel = 0).  With the library's
+default tie tolerance of their format the same points meet the target
+(tests/test_gpu_ties.py).
 """
 import numpy as np
 import pytest
@@ -87,14 +90,14 @@ LARGE = [
                  marks=pytest.mark.xfail(strict=True, reason="int8 with Delta = 2^-2 saturates at "
                                          "31.75 LLR; its LER is below FP64's beyond 3 sigma")),
     pytest.param("point_8", lambda: I.toric3d_point(8), "f16", 2 ** -6, 0.05, 320, 0.015,
-                 marks=pytest.mark.xfail(strict=True, reason="binary16 storage breaks the exact belief "
-                                         "ties of min-sum; its LER is below FP64's beyond 3 sigma")),
+                 marks=pytest.mark.xfail(strict=True, reason="binary16 storage with exact ties breaks the "
+                                         "exact belief ties of min-sum; its LER is below FP64's beyond 3 sigma")),
     pytest.param("point_8", lambda: I.toric3d_point(8), "bf16", 2 ** -6, 0.05, 320, 0.015,
-                 marks=pytest.mark.xfail(strict=True, reason="bfloat16 storage breaks the exact belief "
-                                         "ties of min-sum; its LER is below FP64's beyond 3 sigma")),
+                 marks=pytest.mark.xfail(strict=True, reason="bfloat16 storage with exact ties breaks the "
+                                         "exact belief ties of min-sum; its LER is below FP64's beyond 3 sigma")),
     pytest.param("toric2d_16", lambda: I.toric2d(16), "f16", 2 ** -6, 0.05, 640, 0.06,
-                 marks=pytest.mark.xfail(strict=True, reason="binary16 storage breaks the exact belief "
-                                         "ties of min-sum; its LER is below FP64's beyond 3 sigma")),
+                 marks=pytest.mark.xfail(strict=True, reason="binary16 storage with exact ties breaks the "
+                                         "exact belief ties of min-sum; its LER is below FP64's beyond 3 sigma")),
 ]
 
 
