@@ -125,7 +125,7 @@ struct Plan {
   size_t n_teams = 0;
   std::vector<const lim_code *> codes;
   std::vector<int> code_of_point;
-  std::vector<uint16_t> msg_smem, chk_smem;  // per code
+  std::vector<uint16_t> msg_smem, chk_smem, cst_smem;  // per code
   LaneSizes lane{};
   size_t workspace = 0;
 };
@@ -219,6 +219,7 @@ int make_plan(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_param
     variant = (max_all <= 24 * 1024 && max_E <= 2048) ? LIM_VARIANT_WARP : LIM_VARIANT_CTA;
   pl.msg_smem.assign(pl.codes.size(), 0);
   pl.chk_smem.assign(pl.codes.size(), 0);
+  pl.cst_smem.assign(pl.codes.size(), 0);
   if (variant == LIM_VARIANT_LANE) {
     pl.warp = kKindLane;
     // default: one warp per block, so that as many warps fit on an SM as its
@@ -271,6 +272,7 @@ int make_plan(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_param
       if (streams) cap = std::max(max_bits, std::min(cap, kStreamSmemCap));
     }
     size_t team = max_bits, slot = 0;
+    std::vector<size_t> used_by(pl.codes.size(), 0);
     for (size_t i = 0; i < pl.codes.size(); i++) {
       const CodeLayout &l = lay[i];
       size_t used = l.bits_bytes;
@@ -288,7 +290,19 @@ int make_plan(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_param
       } else {
         slot = std::max(slot, l.msg_bytes + l.chk_bytes);
       }
+      used_by[i] = used;
       team = std::max(team, used);
+    }
+    // The move resolution reads the one-byte move state of every neighbouring
+    // check of a candidate.  When the rest of a code's scratch stays in HBM,
+    // those states alone go to shared memory if they fit in what the team holds
+    // anyway for the other codes: growing the team's shared memory would shrink
+    // the L1 cache that serves the streamed messages (the FP32 2D sweep ran 2 %
+    // slower when the L = 128 states grew each team by 16 KB; the membrane sweep,
+    // whose L = 16 states fit in the room of its smaller codes, 4 % faster).
+    for (size_t i = 0; i < pl.codes.size(); i++) {
+      const size_t cst = ((size_t)pl.codes[i]->dev.m + 15) & ~size_t(15);
+      if (!pl.chk_smem[i] && used_by[i] + cst <= team) pl.cst_smem[i] = 1;
     }
     pl.team_smem = (team + 15) & ~size_t(15);
     pl.smem = pl.team_smem;
@@ -324,6 +338,7 @@ void fill_args(const Plan &pl, const lim_point *pts, uint32_t npts, const lim_pa
     d.point_id = pts[i].point_id;
     d.msg_smem = pl.msg_smem[d.code];
     d.chk_smem = pl.chk_smem[d.code];
+    d.cst_smem = pl.cst_smem[d.code];
     d.p_thr = prob_threshold(pts[i].p);
     d.item0 = item;
     item += pts[i].shots;

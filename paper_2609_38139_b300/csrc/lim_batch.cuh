@@ -717,7 +717,8 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ Lau
     uint8_t *sfree = tsm + Ly.smem_free;
     uint8_t *msg = pt.msg_smem ? sfree : gslot;
     uint8_t *chk = pt.chk_smem ? (pt.msg_smem ? sfree + Ly.msg_bytes : sfree) : gslot + Ly.msg_bytes;
-    const ShotView<T> V = make_view<T>(Ly, tsm, msg, chk);
+    ShotView<T> V = make_view<T>(Ly, tsm, msg, chk);
+    if (pt.cst_smem) V.cstate = pt.msg_smem ? sfree + Ly.msg_bytes : sfree;
     ShotRegs R;
     PhaseClock clk{clock64(), (A.prm.profile && tm.rank() == 0) ? A.tally[pidx].phase_cycles : nullptr};
     shot_init<Team, PREC>(tm, A, pt, C, shot, item, V, R);

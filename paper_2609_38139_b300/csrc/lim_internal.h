@@ -48,6 +48,9 @@ struct DevPoint {
   uint32_t point_id;
   uint16_t msg_smem;   // 1: this code's messages live in shared memory
   uint16_t chk_smem;   // 1: its per-check feedback scratch lives in shared memory
+  uint16_t cst_smem;   // 1: only the scratch's per-check move states live in shared memory
+                       //    (the rest of the scratch in the HBM slot), after the messages
+                       //    when those are in shared memory
   uint64_t p_thr;      // floor(p * 2^32), 2^32 for p >= 1
   uint64_t item0;      // first work item of this point
   uint64_t code_item0; // first item of this point among the items of its code (lane variant)
