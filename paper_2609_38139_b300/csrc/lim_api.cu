@@ -7,6 +7,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -461,6 +462,28 @@ int upload_code(lim_ctx *ctx, HostCode &hc, lim_code **out) {
   else if (h.dc_max <= 4) d.chk_cls = 3;
   else if (h.dc_max <= 6) d.chk_cls = 4;
   else d.chk_cls = 5;
+  // Forward reach of the fused sweep's gathers: a chunk of consecutive check rows
+  // reads its partners' rows, the farthest of which lie pf_rows ahead (2D toric:
+  // L, 3D point sector: L^2) and are read there for the first time in a sweep.
+  d.pf_rows = 0;
+  if (d.dc_u > 0 && d.dv_u > 1 && !h.partner.empty()) {
+    const int np = d.dc_u * (d.dv_u - 1);
+    std::map<int32_t, int64_t> count;
+    for (int32_t c = 0; c < h.m; c++) {
+      int32_t far = 0;
+      for (int j = 0; j < np; j++) {
+        const int32_t dist = h.partner[(size_t)c * np + j] / d.dc_u - c;
+        if (dist > 0 && dist < h.m / 2) far = std::max(far, dist);
+      }
+      count[far]++;
+    }
+    int64_t best = 0;
+    for (const auto &kv : count)
+      if (kv.first > 0 && kv.second > best) {
+        best = kv.second;
+        d.pf_rows = kv.first;
+      }
+  }
   if (ctx->device < 0) {  // host-only context
     *out = c;
     return LIM_OK;

@@ -699,13 +699,23 @@ __device__ __forceinline__ void fused_loop(int rank, int size, const DevCode &C,
   }
 }
 
+// TMA bulk prefetch of [p, p + bytes) into L2 (no registers, no shared memory,
+// no completion to wait for); p and bytes multiples of 16.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // The same with dynamic work distribution for a block team: warps take chunks of
 // 32*NB checks from a shared counter (reset to 0 before the pass), so warps that
-// finish early take more work instead of waiting at the barrier.
+// finish early take more work instead of waiting at the barrier.  With pf_ahead
+// > 0 (messages in global memory) the warp that takes chunk k asks L2 for the
+// rows that chunk k + pf_ahead reads for the first time in this sweep, the rows
+// pf_rows ahead of it, so that those gathers find L2 instead of waiting on DRAM.
 template <int PREC, int RULE, int DC, int DV, int NB, class SBit>
 __device__ __forceinline__ void fused_loop_dyn(int32_t *work, const DevCode &C, const DevParams &P,
                                                const SBit &sbit, const typename MT<PREC>::T *CVp,
-                                               typename MT<PREC>::T *CVn) {
+                                               typename MT<PREC>::T *CVn, int pf_ahead) {
+  using T = typename MT<PREC>::T;
   const int lane = threadIdx.x & 31;
   constexpr int CH = 32 * NB;
   for (;;) {
@@ -714,6 +724,17 @@ __device__ __forceinline__ void fused_loop_dyn(int32_t *work, const DevCode &C, 
     chunk = __shfl_sync(0xffffffffu, chunk, 0);
     const int c0 = chunk * CH;
     if (c0 >= C.m) break;
+    if (pf_ahead > 0 && lane == 0) {
+      const int r0 = c0 + pf_ahead * CH + C.pf_rows;
+      if (r0 < C.m) {
+        const int r1 = min(C.m, r0 + CH);
+        // byte range of rows [r0, r1) widened to 16-byte boundaries; the buffer
+        // is padded to a multiple of 16 bytes, so the range stays inside it
+        const size_t b0 = ((size_t)r0 * DC * sizeof(T)) & ~size_t(15);
+        const size_t b1 = ((size_t)r1 * DC * sizeof(T) + 15) & ~size_t(15);
+        prefetch_l2_bulk(reinterpret_cast<const uint8_t *>(CVp) + b0, (uint32_t)(b1 - b0));
+      }
+    }
     if (c0 + CH <= C.m) {
       FusedIn<PREC, DC, DV> g[NB];
 #pragma unroll
@@ -762,7 +783,12 @@ __device__ __noinline__ void fused_run(int rank, int size, const DevCode &C, con
   // (12 gathered values, warp teams) one at a time, which keeps spills down (+11 %)
   constexpr int NB = SMEM ? (NP <= 6 ? 2 : 1)
                         : (NP <= 4 ? 4 : (NP <= 6 ? (RULE == LIM_RULE_MINSUM ? 3 : 2) : (DC == 4 ? 2 : 1)));
-  if (work && (!SMEM || C.m >= 2 * size)) fused_loop_dyn<PREC, RULE, DC, DV, NB>(work, C, P, sbit, CVp, CVn);
+  // prefetch half a round of the team's warps ahead (global-memory messages
+  // only): on the 2D sweep half a round, one round and two rounds ran within 3 %
+  // of one another, half a round fastest
+  const int pf_ahead = (!SMEM && C.pf_rows > 0) ? max(1, size >> 6) : 0;
+  if (work && (!SMEM || C.m >= 2 * size))
+    fused_loop_dyn<PREC, RULE, DC, DV, NB>(work, C, P, sbit, CVp, CVn, pf_ahead);
   else fused_loop<PREC, RULE, DC, DV, NB>(rank, size, C, P, sbit, CVp, CVn);
 }
 

@@ -32,6 +32,9 @@ struct DevCode {
   int32_t dv_u, dc_u;          // uniform qubit / check degree, 0 if irregular
   const int32_t *partner;      // [E*(dv_u-1)]: a qubit's other edges per edge (uniform
                                // degrees), ascending check order, or null
+  int32_t pf_rows;             // rows from a check row to its farthest partner row ahead,
+                               // the most common such distance (wrap-around excluded);
+                               // 0: none.  The global-memory sweep prefetches there.
   const int32_t *c_ptr;        // [m+1]
   const int32_t *c_var;        // [E]
   const int32_t *v_ptr;        // [n+1]
