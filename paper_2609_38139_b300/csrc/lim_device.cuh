@@ -784,8 +784,8 @@ __device__ __noinline__ void fused_run(int rank, int size, const DevCode &C, con
   constexpr int NB = SMEM ? (NP <= 6 ? 2 : 1)
                         : (NP <= 4 ? 4 : (NP <= 6 ? (RULE == LIM_RULE_MINSUM ? 3 : 2) : (DC == 4 ? 2 : 1)));
   // prefetch half a round of the team's warps ahead (global-memory messages
-  // only): on the 2D sweep half a round, one round and two rounds ran within 3 %
-  // of one another, half a round fastest
+  // only): of half a round, one round and two rounds ahead, half a round ran
+  // fastest on the 2D sweep and two rounds slowest
   const int pf_ahead = (!SMEM && C.pf_rows > 0) ? max(1, size >> 6) : 0;
   if (work && (!SMEM || C.m >= 2 * size))
     fused_loop_dyn<PREC, RULE, DC, DV, NB>(work, C, P, sbit, CVp, CVn, pf_ahead);
