@@ -34,7 +34,7 @@ def ctx(L):
     return L.Context(0)
 
 
-def _workload_sample(L, ctx, workload, prec, picks, seed=0, shot0=7000):
+def _workload_sample(L, ctx, workload, prec, picks, seed=0, shot0=7000, shape=(0, 0)):
     """One launch over every code of ``workload`` (as the benchmark builds them),
     with ``picks`` = {size: [(p, shots), ...]} shots; every code of the workload
     is present (sizes without picks get one shot at their first p), so the plan
@@ -44,7 +44,8 @@ def _workload_sample(L, ctx, workload, prec, picks, seed=0, shot0=7000):
     prm = L.params(rule=w.get("rule", "minsum"), feedback=w.get("feedback", "check_move"),
                    precision=prec, quant_scale=qs, q=w["q"], clamp=w["clamp"], tau=w["tau"],
                    dt_tick=w["dt_tick"], sweeps_per_tick=w["K"], tick_budget=1,
-                   tie_rel=L.default_tie_rel(prec, w.get("rule", "minsum")))
+                   tie_rel=L.default_tie_rel(prec, w.get("rule", "minsum")),
+                   block_threads=shape[0], blocks_per_sm=shape[1])
     pts, meta = [], []
     pid = 0
     for size in w["sizes"]:
@@ -110,3 +111,18 @@ def test_full_size_bb_i8(L, ctx):
              (12, 6): [(0.01, 8), (0.08, 8)]}
     n = _workload_sample(L, ctx, "bb_mixed", "i8", picks)
     assert n == 48
+
+
+@pytest.mark.parametrize("workload,prec,picks", [
+    ("toric2d_sweep", "f32", {128: [(0.02, 1), (0.12, 1)], 64: [(0.08, 2)]}),
+    ("toric2d_sweep", "f16", {128: [(0.12, 1)], 64: [(0.08, 1)]}),
+    ("toric2d_sweep", "i16", {128: [(0.02, 1)], 64: [(0.08, 1)]}),
+    ("toric3d_point_sweep", "bf16", {24: [(0.05, 1)], 16: [(0.03, 1)]}),
+], ids=["2d-f32", "2d-f16", "2d-i16", "point-bf16"])
+def test_full_size_in_the_tuned_shape(L, ctx, workload, prec, picks):
+    """The shape lim_autotune picks for these sweeps in the benchmark (five 192-thread
+    teams per SM), whose global-memory sweep prefetches its first-touch rows into L2
+    three chunks ahead (the library default shape prefetches eight ahead): the same
+    records and final residuals as the oracle."""
+    n = _workload_sample(L, ctx, workload, prec, picks, shape=(192, 5))
+    assert n >= 2
