@@ -259,7 +259,9 @@ int lim_workspace_size(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const 
  * launch (variant PLAIN: one launch per tick).  Work items are the (point, shot)
  * pairs, handed out from a device queue in point order, so list the most
  * expensive points first.
- *   workspace  device, >= lim_workspace_size() bytes (contents not preserved)
+ *   workspace  device, >= lim_workspace_size() bytes (contents not preserved),
+ *              256-byte aligned (as cudaMalloc returns; else LIM_E_INVAL).  The
+ *              same holds for every workspace argument below.
  *   rec        device, nullable: one lim_shot_record per shot, points in order
  *   e_final    device, nullable: final residual bits, one row of
  *              max_n_words words per shot (same order as rec)

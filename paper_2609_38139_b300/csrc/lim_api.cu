@@ -38,6 +38,9 @@ void set_error(const std::string &msg) { g_last_error = msg; }
 namespace {
 
 constexpr size_t kWsHeader = 4096;  // queue counter + a tally used by lim_trace
+constexpr size_t kWsAlign = 256;    // required alignment of a caller-given workspace (the team
+                                     // slots inside it take 16-byte vector accesses and bulk
+                                     // prefetches; cudaMalloc and torch return 256-byte aligned)
 constexpr size_t kStreamSmemCap = 160 * 1024;  // shared memory per block when a code streams from HBM
 
 int cuda_fail(cudaError_t err, const char *what) {
@@ -739,6 +742,7 @@ int run_batch(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const lim_param
               uint64_t seed, const uint32_t *e0, void *workspace, size_t workspace_bytes,
               lim_shot_record *rec, uint32_t *e_final, lim_tally *tally, void *stream) {
   if (!tally || !workspace) return bad(LIM_E_INVAL, "null tally or workspace");
+  if (reinterpret_cast<uintptr_t>(workspace) % kWsAlign) return bad(LIM_E_INVAL, "workspace not 256-byte aligned");
   DevParams dp;
   int st = derive(prm, dp);
   if (st) return st;
@@ -834,6 +838,7 @@ int lim_run_batch_host(lim_ctx *ctx, const lim_point *pts, uint32_t npts, const 
                        lim_tally *tally_host, void *stream) {
   return guarded([&] {
     if (!tally_host || !workspace) return bad(LIM_E_INVAL, "null tally or workspace");
+    if (reinterpret_cast<uintptr_t>(workspace) % kWsAlign) return bad(LIM_E_INVAL, "workspace not 256-byte aligned");
     if (prm && prm->variant == LIM_VARIANT_PLAIN)
       return bad(LIM_E_UNSUPPORTED, "lim_run_batch_host runs the persistent kernel only");
     HostStaging hs;
@@ -896,6 +901,7 @@ int lim_graph_create_from(lim_ctx *ctx, const lim_point *pts, uint32_t npts, con
                           lim_graph **out) {
   return guarded([&] {
     if (!out || !tally || !workspace) return bad(LIM_E_INVAL, "null argument");
+    if (reinterpret_cast<uintptr_t>(workspace) % kWsAlign) return bad(LIM_E_INVAL, "workspace not 256-byte aligned");
     DevParams dp;
     int st = derive(prm, dp);
     if (st) return st;
@@ -1121,6 +1127,7 @@ int lim_trace(lim_ctx *ctx, const lim_code *code, const lim_params *prm, double 
               uint32_t *s_hist, float *l_hist, lim_shot_record *rec, void *stream) {
   return guarded([&] {
     if (!code || !e_hist || !s_hist || !workspace || max_ticks < 0) return bad(LIM_E_INVAL, "bad argument");
+    if (reinterpret_cast<uintptr_t>(workspace) % kWsAlign) return bad(LIM_E_INVAL, "workspace not 256-byte aligned");
     if (nforced < 0 || (nforced > 0 && !forced_moves)) return bad(LIM_E_INVAL, "bad forced moves");
     DevParams dp;
     int st = derive(prm, dp);

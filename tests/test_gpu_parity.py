@@ -601,3 +601,28 @@ def test_autotuner_picks_a_working_shape(L, ctx):
     _, rec_a = L.run_batch(ctx, pts, prm, 5)
     _, rec_b = L.run_batch(ctx, pts, best, 5)
     assert np.array_equal(rec_a, rec_b)  # the shape never changes results
+
+
+def test_misaligned_workspace_is_refused(L, ctx):
+    """A workspace that is not 256-byte aligned is refused (LIM_E_INVAL) before
+    anything is launched; the same buffer at its aligned start runs."""
+    import ctypes
+    code = ctx.from_inputs(I.toric2d(8))
+    prm = L.params(precision="f32", tick_budget=8)
+    pts = [(code, 0.05, 4, 0, 0)]
+    arr = L._points(pts)
+    ws_bytes = L.workspace_size(ctx, pts, prm)
+    buf = torch.empty(ws_bytes + 512, dtype=torch.uint8, device="cuda")
+    assert buf.data_ptr() % 256 == 0
+    tally = torch.zeros(L.TALLY_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    for off in (16, 128):
+        st = L.lib().lim_run_batch(ctx.handle, arr, 1, ctypes.byref(prm), 1, buf.data_ptr() + off,
+                                   ws_bytes, None, None, tally.data_ptr(), None)
+        assert L.STATUS[st] == "LIM_E_INVAL", st
+        assert "aligned" in L.lib().lim_last_error().decode()
+    st = L.lib().lim_run_batch(ctx.handle, arr, 1, ctypes.byref(prm), 1, buf.data_ptr(), ws_bytes,
+                               None, None, tally.data_ptr(), None)
+    assert st == 0
+    torch.cuda.synchronize()
+    t = np.frombuffer(tally.cpu().numpy().tobytes(), dtype=L.TALLY_DTYPE)
+    assert int(t["shots"][0]) == 4 and int(t["errors"][0]) == 0
